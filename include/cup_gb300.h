@@ -1,0 +1,176 @@
+/*
+ * cup_gb300.h — C ABI of the GB300 (sm_103a) CUP library over prime fields.
+ *
+ * The library computes the rank-profile revealing CUP decomposition of
+ * Jeannerod, Pernet and Storjohann ("Rank-profile revealing Gaussian
+ * elimination and the CUP matrix decomposition") and the problems the paper
+ * reduces to it, over GF(p) for a prime p < 2^31, with hand-written CUDA
+ * kernels on one GPU.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Matrices are caller-owned DEVICE buffers of uint32 residues in [0, p),
+ *   row-major with a leading dimension ld >= number of columns (zero-based
+ *   indices and half-open ranges, Sec. 1.1). The library never frees them.
+ * - Index outputs (rank profile, pivots) are caller-owned DEVICE int64 arrays.
+ * - Scalars returned through plain pointers (rank, determinant) are HOST
+ *   pointers; a call that returns one synchronises `stream` before returning.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream). Work is enqueued on it; buffers must stay valid until it drains.
+ * - The handle owns all temporary device memory (the pivot-phase scratch of
+ *   the base case, the transposition lists and the 8-bit limb planes of the
+ *   tensor-core products), as Definition 1 allows for matrix products. Calls on
+ *   one handle must not overlap: use one handle per concurrent stream.
+ * - Nothing throws across the ABI; every call returns a cup_status. On an
+ *   error the contents of output buffers are unspecified, except that
+ *   CUP_SINGULAR from cup_inverse leaves A holding the [C\U] factors.
+ */
+#ifndef CUP_GB300_H
+#define CUP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CUP_OK = 0,
+    CUP_SINGULAR = 1,          /* square input of rank < n (cup_inverse) */
+    CUP_INCONSISTENT = 2,      /* cup_solve: the right-hand side is not in the column space */
+    CUP_ERR_ARG = -1,          /* bad size, leading dimension, null pointer or option */
+    CUP_ERR_PRIME = -2,        /* p is not a prime below 2^31 */
+    CUP_ERR_VALUE = -3,        /* an entry >= p (only checked when validation is on) */
+    CUP_ERR_CUDA = -4,         /* a CUDA call failed (see cup_last_cuda_error) */
+    CUP_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired */
+    CUP_ERR_NOMEM = -6,        /* workspace allocation failed */
+    CUP_ERR_UNSUPPORTED = -7   /* valid request this build cannot serve */
+} cup_status;
+
+typedef struct cup_handle cup_handle;
+
+/* Engine used for the Schur update C <- C - A B mod p (Algorithm 1 with
+ * alpha = -1, beta = 1, Sec. 3.2): */
+enum {
+    CUP_ENGINE_PLAIN = 0,      /* CUDA-core 64-bit integer multiply and reduce */
+    CUP_ENGINE_TENSOR = 1      /* tcgen05 tensor cores on exact 8-bit limbs */
+};
+
+/* Options for cup_set_option. */
+enum {
+    CUP_OPT_ENGINE = 0,        /* CUP_ENGINE_PLAIN or CUP_ENGINE_TENSOR (default TENSOR) */
+    CUP_OPT_LEAF_ROWS = 1,     /* rows of a base-case slab, 1..64 (default 32) */
+    CUP_OPT_WINDOW = 2,        /* pivot-search window of the base case, 1..128 (default 64) */
+    CUP_OPT_TC_MIN_K = 3,      /* smallest inner dimension sent to the tensor engine */
+    CUP_OPT_VALIDATE = 4       /* nonzero: check inputs are canonical residues (slow) */
+};
+
+/* Create a handle bound to CUDA device `device` (the device is made current
+ * for the duration of each call). */
+cup_status cup_create(cup_handle **handle, int device);
+
+/* Release a handle and all its workspace. */
+cup_status cup_destroy(cup_handle *handle);
+
+/* Set an option (see the CUP_OPT_* list). */
+cup_status cup_set_option(cup_handle *handle, int option, int64_t value);
+
+/* Text of the last CUDA error seen by this handle (static storage). */
+const char *cup_last_cuda_error(cup_handle *handle);
+
+/*
+ * CUP decomposition in place (Algorithm 6, Sec. 3.3; Ensures: A <- [C\U]).
+ *   A        m x n device matrix (lda), overwritten by the space-sharing
+ *            storage [C\U] of Sec. 3.1: rows 0..r-1 hold U strictly above the
+ *            diagonal (U is unit upper triangular, its diagonal implicit); C's
+ *            first r columns are stored on and below the diagonal; all other
+ *            entries are zero. A P^T = C U with U embedded in an n x n unit
+ *            upper triangular matrix.
+ *   d_profile device int64[min(m,n)]: entries 0..r-1 receive the row rank
+ *            profile i_0 < ... < i_{r-1} (Sec. 2).
+ *   d_ipiv   device int64[min(m,n)]: entries 0..r-1 receive the column
+ *            transpositions, LAPACK style: P = T_{r-1,ipiv[r-1]} ... T_{0,ipiv[0]},
+ *            i.e. A P^T applies the swaps (t, ipiv[t]) to columns for
+ *            t = 0, 1, ..., r-1 in order, with ipiv[t] >= t.
+ *   rank     host int64*: receives r (the call synchronises `stream`).
+ * The pivot of each row is the first nonzero of its residual at a position
+ * >= the current rank, transposed with that position (the rule of
+ * Algorithm 6's base case), so C, U and P are those that rule defines.
+ */
+cup_status cup_factor(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda,
+                      uint32_t p, int64_t *d_profile, int64_t *d_ipiv, int64_t *rank,
+                      void *stream);
+
+/*
+ * Rank and row rank profile (Sec. 2; Prop. 3). A is destroyed (it receives
+ * the [C\U] factors). d_profile as in cup_factor.
+ */
+cup_status cup_rank_profile(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda,
+                            uint32_t p, int64_t *d_profile, int64_t *rank, void *stream);
+
+/*
+ * Determinant of a square matrix (Sec. 5: CUP suffices). A is destroyed.
+ * *det receives det(A) mod p: 0 if the rank is below n, otherwise the
+ * product of C's diagonal (the pivots) times (-1)^(number of nontrivial
+ * transpositions).
+ */
+cup_status cup_det(cup_handle *handle, uint32_t *A, int64_t n, int64_t lda, uint32_t p,
+                   uint32_t *det, void *stream);
+
+/*
+ * In-place inverse of a square matrix (Algorithm 8 via Algorithm 7 and the
+ * TRSM/TRTRI/TRULM building blocks, Sec. 3.5 and Sec. 4.3). On success A
+ * holds A^{-1}. Returns CUP_SINGULAR (A holds the [C\U] factors) if the rank
+ * is below n.
+ */
+cup_status cup_inverse(cup_handle *handle, uint32_t *A, int64_t n, int64_t lda, uint32_t p,
+                       void *stream);
+
+/*
+ * Reduced column echelon form (Proposition 1, Algorithm 8): A (m x n) is
+ * overwritten by R, the unique reduced column echelon form of A (columns
+ * >= r zero). d_profile as in cup_factor. If X is not NULL it is an n x n
+ * device matrix (ldx) that receives the transform with A X = R
+ * (X = P^T [X1 X2; 0 I] of Algorithm 8, unique given P).
+ */
+cup_status cup_rref(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                    int64_t *d_profile, int64_t *rank, uint32_t *X, int64_t ldx, void *stream);
+
+/*
+ * Linear system A X = B (Sec. 5: solving reduces to CUP). A (m x n) is
+ * destroyed; B (m x k, ldb) is read and destroyed; X (n x k, ldx) receives
+ * the solution whose entries outside the CUP pivot columns are zero
+ * (x = P^T [U1^{-1} L1^{-1} b_profile; 0]). Returns CUP_INCONSISTENT when no
+ * solution exists. *rank receives r.
+ */
+cup_status cup_solve(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda,
+                     uint32_t *B, int64_t k, int64_t ldb, uint32_t *X, int64_t ldx, uint32_t p,
+                     int64_t *rank, void *stream);
+
+/* ---- Building blocks of the hot path (exposed for testing and reuse) ---- */
+
+/* Schur update (Algorithm 1, alpha = -1, beta = 1): C <- C - A B mod p.
+ * A is M x K (lda), B is K x N (ldb), C is M x N (ldc); C must not overlap A
+ * or B. `engine` selects CUP_ENGINE_PLAIN or CUP_ENGINE_TENSOR. */
+cup_status cup_mm_sub(cup_handle *handle, uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                      const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K, uint32_t p,
+                      int engine, void *stream);
+
+/* TRSM(Right, Upper, Unit) (Algorithm 2, unit-diagonal variant, as used by
+ * Algorithm 6's TRSM step): B <- B U^{-1}. U is n x n (ldu); only its strict
+ * upper triangle is read. B is m x n (ldb). */
+cup_status cup_trsm_ruu(cup_handle *handle, const uint32_t *U, int64_t ldu, uint32_t *B,
+                        int64_t ldb, int64_t m, int64_t n, uint32_t p, void *stream);
+
+/* Column transpositions (Sec. 1.1): for t = k0..k1-1 in order, swap columns t
+ * and d_ipiv[t] of rows row0..row0+nrows-1 of A (A <- A P^T restricted to
+ * those transpositions). d_ipiv is a device array indexed by absolute
+ * position. */
+cup_status cup_laswp_cols(cup_handle *handle, uint32_t *A, int64_t lda, int64_t row0,
+                          int64_t nrows, const int64_t *d_ipiv, int64_t k0, int64_t k1,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUP_GB300_H */

@@ -1,0 +1,291 @@
+"""Python binding of the GB300 CUP library (ctypes over include/cup_gb300.h).
+
+Argument marshalling only: every step of every call runs in the CUDA kernels
+of libcup_gb300.so. PyTorch supplies device memory and the current stream.
+Residues are held in torch.int32 tensors (values in [0, p) with p < 2^31 are
+non-negative, so the bits equal the uint32 the library reads) and index
+arrays in torch.int64 tensors. There is no CPU fallback: if the library is
+missing or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = ["load", "Handle", "factor", "rank_profile", "det", "inverse", "rref", "solve",
+           "mm_sub", "trsm_ruu", "laswp_cols", "ENGINE_PLAIN", "ENGINE_TENSOR", "CupError",
+           "LIB_PATH"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcup_gb300.so")
+
+ENGINE_PLAIN = 0
+ENGINE_TENSOR = 1
+OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE = 0, 1, 2, 3, 4
+
+STATUS = {0: "CUP_OK", 1: "CUP_SINGULAR", 2: "CUP_INCONSISTENT", -1: "CUP_ERR_ARG",
+          -2: "CUP_ERR_PRIME", -3: "CUP_ERR_VALUE", -4: "CUP_ERR_CUDA", -5: "CUP_ERR_TIMEOUT",
+          -6: "CUP_ERR_NOMEM", -7: "CUP_ERR_UNSUPPORTED"}
+
+# Every entry point of include/cup_gb300.h with its ctypes signature.
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_U32 = ctypes.c_uint32
+_INT = ctypes.c_int
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+SIGNATURES = {
+    "cup_create": (_INT, [ctypes.POINTER(_P), _INT]),
+    "cup_destroy": (_INT, [_P]),
+    "cup_set_option": (_INT, [_P, _INT, _I64]),
+    "cup_last_cuda_error": (ctypes.c_char_p, [_P]),
+    "cup_factor": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
+    "cup_rank_profile": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P]),
+    "cup_det": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
+    "cup_inverse": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
+    "cup_rref": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P, _I64, _P]),
+    "cup_solve": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P, _I64, _U32, _I64P, _P]),
+    "cup_mm_sub": (_INT, [_P, _P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _INT, _P]),
+    "cup_trsm_ruu": (_INT, [_P, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
+    "cup_laswp_cols": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P]),
+}
+
+_lib = None
+
+
+class CupError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+def load(path: str | None = None):
+    """Load libcup_gb300.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _mat(t, what):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype not in (torch.int32,):
+        raise TypeError(f"{what} must be torch.int32 holding residues in [0, p)")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{what} must be a row-major 2-D tensor (unit column stride)")
+    return t.shape[0], t.shape[1], max(t.stride(0), 1)
+
+
+class Handle:
+    """Owns a cup_handle (and its device workspace) for one CUDA device."""
+
+    def __init__(self, device: int | None = None, engine: int | None = None, **opts):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the CUP library has no CPU path")
+        self.lib = load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        self._check(self.lib.cup_create(ctypes.byref(h), self.device), "cup_create", None)
+        self.h = h
+        if engine is not None:
+            self.set_option(OPT_ENGINE, engine)
+        names = {"leaf_rows": OPT_LEAF_ROWS, "window": OPT_WINDOW, "tc_min_k": OPT_TC_MIN_K,
+                 "validate": OPT_VALIDATE}
+        for k, v in opts.items():
+            self.set_option(names[k], int(v))
+
+    def _check(self, st, what, h):
+        if st not in (0,):
+            detail = ""
+            if h is not None and st == -4:
+                detail = self.lib.cup_last_cuda_error(h).decode()
+            raise CupError(st, what, detail)
+
+    def set_option(self, opt: int, value: int):
+        self._check(self.lib.cup_set_option(self.h, opt, int(value)), "cup_set_option", self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cup_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- entry points -----------------------------------------------------
+    def factor(self, A, p: int, stream=None):
+        """In-place CUP (Algorithm 6): A <- [C\\U]; returns (rank, profile, ipiv)
+        with profile/ipiv int64 device tensors of length min(m, n) (first rank valid)."""
+        torch = _torch()
+        m, n, lda = _mat(A, "A")
+        k = max(min(m, n), 1)
+        prof = torch.empty(k, dtype=torch.int64, device=A.device)
+        ipiv = torch.empty(k, dtype=torch.int64, device=A.device)
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_factor(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(),
+                                 ipiv.data_ptr(), ctypes.byref(r), _stream_ptr(stream))
+        self._check(st, "cup_factor", self.h)
+        return r.value, prof, ipiv
+
+    def rank_profile(self, A, p: int, stream=None):
+        torch = _torch()
+        m, n, lda = _mat(A, "A")
+        prof = torch.empty(max(min(m, n), 1), dtype=torch.int64, device=A.device)
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_rank_profile(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(),
+                                       ctypes.byref(r), _stream_ptr(stream))
+        self._check(st, "cup_rank_profile", self.h)
+        return r.value, prof[: r.value]
+
+    def det(self, A, p: int, stream=None) -> int:
+        n, n2, lda = _mat(A, "A")
+        if n != n2:
+            raise ValueError("det needs a square matrix")
+        d = ctypes.c_uint32(0)
+        st = self.lib.cup_det(self.h, A.data_ptr(), n, lda, p, ctypes.byref(d), _stream_ptr(stream))
+        self._check(st, "cup_det", self.h)
+        return int(d.value)
+
+    def inverse(self, A, p: int, stream=None) -> bool:
+        """A <- A^{-1} in place; returns False (A holds [C\\U]) if A is singular."""
+        n, n2, lda = _mat(A, "A")
+        if n != n2:
+            raise ValueError("inverse needs a square matrix")
+        st = self.lib.cup_inverse(self.h, A.data_ptr(), n, lda, p, _stream_ptr(stream))
+        if st == 1:
+            return False
+        self._check(st, "cup_inverse", self.h)
+        return True
+
+    def rref(self, A, p: int, want_x: bool = False, stream=None):
+        """A <- R (reduced column echelon form); returns (rank, profile, X or None)."""
+        torch = _torch()
+        m, n, lda = _mat(A, "A")
+        prof = torch.empty(max(min(m, n), 1), dtype=torch.int64, device=A.device)
+        X = torch.empty((n, n), dtype=torch.int32, device=A.device) if want_x else None
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_rref(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(), ctypes.byref(r),
+                               X.data_ptr() if want_x else None, n if want_x else 0,
+                               _stream_ptr(stream))
+        self._check(st, "cup_rref", self.h)
+        return r.value, prof[: r.value], X
+
+    def solve(self, A, B, p: int, stream=None):
+        """Solve A X = B; returns (status, X, rank) with status 0 or 2 (inconsistent)."""
+        torch = _torch()
+        m, n, lda = _mat(A, "A")
+        mb, k, ldb = _mat(B, "B")
+        if mb != m:
+            raise ValueError("B must have as many rows as A")
+        X = torch.zeros((n, k), dtype=torch.int32, device=A.device)
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_solve(self.h, A.data_ptr(), m, n, lda, B.data_ptr(), k, ldb,
+                                X.data_ptr(), max(k, 1), p, ctypes.byref(r), _stream_ptr(stream))
+        if st == 2:
+            return 2, X, r.value
+        self._check(st, "cup_solve", self.h)
+        return 0, X, r.value
+
+    def mm_sub(self, C, A, B, p: int, engine: int = ENGINE_TENSOR, stream=None):
+        """C <- C - A B mod p (Algorithm 1 with alpha = -1, beta = 1)."""
+        M, N, ldc = _mat(C, "C")
+        M2, K, lda = _mat(A, "A")
+        K2, N2, ldb = _mat(B, "B")
+        if (M2, K2, N2) != (M, K, N):
+            raise ValueError("shape mismatch")
+        st = self.lib.cup_mm_sub(self.h, C.data_ptr(), ldc, A.data_ptr(), lda, B.data_ptr(), ldb,
+                                 M, N, K, p, engine, _stream_ptr(stream))
+        self._check(st, "cup_mm_sub", self.h)
+
+    def trsm_ruu(self, U, B, p: int, stream=None):
+        """B <- B U^{-1}, U unit upper triangular (strict upper part read)."""
+        n, n2, ldu = _mat(U, "U")
+        m, nb, ldb = _mat(B, "B")
+        if n != n2 or nb != n:
+            raise ValueError("shape mismatch")
+        st = self.lib.cup_trsm_ruu(self.h, U.data_ptr(), ldu, B.data_ptr(), ldb, m, n, p,
+                                   _stream_ptr(stream))
+        self._check(st, "cup_trsm_ruu", self.h)
+
+    def laswp_cols(self, A, ipiv, k0: int, k1: int, row0: int = 0, nrows: int | None = None,
+                   stream=None):
+        m, n, lda = _mat(A, "A")
+        nrows = m - row0 if nrows is None else nrows
+        st = self.lib.cup_laswp_cols(self.h, A.data_ptr(), lda, row0, nrows, ipiv.data_ptr(),
+                                     k0, k1, _stream_ptr(stream))
+        self._check(st, "cup_laswp_cols", self.h)
+
+
+_default = {}
+
+
+def _handle(engine=None) -> Handle:
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    key = (dev, engine)
+    if key not in _default:
+        _default[key] = Handle(dev, engine=engine)
+    return _default[key]
+
+
+def factor(A, p, engine=None, stream=None):
+    return _handle(engine).factor(A, p, stream)
+
+
+def rank_profile(A, p, engine=None, stream=None):
+    return _handle(engine).rank_profile(A, p, stream)
+
+
+def det(A, p, engine=None, stream=None):
+    return _handle(engine).det(A, p, stream)
+
+
+def inverse(A, p, engine=None, stream=None):
+    return _handle(engine).inverse(A, p, stream)
+
+
+def rref(A, p, want_x=False, engine=None, stream=None):
+    return _handle(engine).rref(A, p, want_x, stream)
+
+
+def solve(A, B, p, engine=None, stream=None):
+    return _handle(engine).solve(A, B, p, stream)
+
+
+def mm_sub(C, A, B, p, engine=ENGINE_TENSOR, stream=None):
+    return _handle().mm_sub(C, A, B, p, engine, stream)
+
+
+def trsm_ruu(U, B, p, stream=None):
+    return _handle().trsm_ruu(U, B, p, stream)
+
+
+def laswp_cols(A, ipiv, k0, k1, row0=0, nrows=None, stream=None):
+    return _handle().laswp_cols(A, ipiv, k0, k1, row0, nrows, stream)

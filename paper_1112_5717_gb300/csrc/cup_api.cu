@@ -1,0 +1,414 @@
+// Host driver and C ABI of the CUP library (declared in include/cup_gb300.h).
+//
+// cup_factor follows the row-recursive structure of Algorithm 6 (Sec. 3.3):
+// split the rows, factor the top block (rec1), transpose the bottom block's
+// columns (A2 <- A2 P1^T), TRSM(Right, Upper, Unit) on its first r1 columns,
+// Schur update H <- A22 - G V1, factor H (rec2), transpose V1's columns
+// (V1 <- V1 P2^T). The leaves are slabs of at most CUP_BMAX rows factored by
+// the base-case kernels. Differences from the printed algorithm, all of which
+// leave C, U, P, the rank and the profile unchanged:
+//   * U's rows are written by the leaves straight to their final rows of the
+//     [C\U] storage (global rows col0..col0+r-1, where col0 is the rank of
+//     the rows above), so the row-move loop of Algorithm 6 is not needed;
+//   * the split point is aligned to the leaf size instead of floor(m/2), and a
+//     leaf may split itself again where its pivot window runs out (any split
+//     point yields the same decomposition);
+//   * P and the rank profile are stored with absolute indices as they are
+//     found, so P <- Diag(I_r1, P2) P1 and the profile offsets need no work.
+#include <cstdio>
+#include <cstring>
+#include <cstdlib>
+#include <new>
+#include "cup_internal.cuh"
+#include "../../include/cup_gb300.h"
+
+struct cup_handle {
+    int device = 0;
+    int engine = CUP_ENGINE_PLAIN;
+    int leaf_rows = 32;
+    int window = 64;
+    int64_t tc_min_k = 256;
+    int validate = 0;
+    SlabScratch *d_slab = nullptr;
+    int2 *d_pairs = nullptr;
+    int64_t pairs_cap = 0;
+    int *d_count = nullptr;
+    int *h_pinned = nullptr;
+    char err[256] = {0};
+};
+
+namespace {
+
+cup_status cuda_ok(cup_handle *h, cudaError_t e)
+{
+    if (e == cudaSuccess) return CUP_OK;
+    snprintf(h->err, sizeof(h->err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? CUP_ERR_NOMEM : CUP_ERR_CUDA;
+}
+
+#define CK(x)                                  \
+    do {                                       \
+        cup_status _s = (x);                   \
+        if (_s != CUP_OK) return _s;           \
+    } while (0)
+#define CU(x) CK(cuda_ok(h, (x)))
+
+uint64_t powmod64(uint64_t b, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    b %= m;
+    while (e) {
+        if (e & 1) r = (uint64_t)((unsigned __int128)r * b % m);
+        b = (uint64_t)((unsigned __int128)b * b % m);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Deterministic Miller-Rabin for 32-bit n (bases 2, 3, 5, 7 suffice below 3.2e9).
+bool is_prime32(uint32_t n)
+{
+    if (n < 2) return false;
+    for (uint32_t q : {2u, 3u, 5u, 7u}) {
+        if (n % q == 0) return n == q;
+    }
+    uint32_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (uint32_t a : {2u, 3u, 5u, 7u}) {
+        uint64_t x = powmod64(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int i = 1; i < s; ++i) {
+            x = x * x % n;
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+cup_status check_prime(uint32_t p)
+{
+    if (p >= (1u << 31) || !is_prime32(p)) return CUP_ERR_PRIME;
+    return CUP_OK;
+}
+
+struct Ctx {
+    cup_handle *h;
+    uint32_t *A;
+    int64_t lda, n;
+    ModP M;
+    int64_t *ipiv, *prof;
+    cudaStream_t st;
+};
+
+cup_status ensure_pairs(cup_handle *h, int64_t need)
+{
+    if (need <= h->pairs_cap) return CUP_OK;
+    if (h->d_pairs) cudaFree(h->d_pairs);
+    h->d_pairs = nullptr;
+    h->pairs_cap = 0;
+    CU(cudaMalloc(&h->d_pairs, (size_t)need * sizeof(int2)));
+    h->pairs_cap = need;
+    return CUP_OK;
+}
+
+cup_status ensure_base(cup_handle *h)
+{
+    if (!h->d_slab) CU(cudaMalloc(&h->d_slab, sizeof(SlabScratch)));
+    if (!h->d_count) CU(cudaMalloc(&h->d_count, sizeof(int)));
+    if (!h->h_pinned) CU(cudaMallocHost(&h->h_pinned, 16 * sizeof(int)));
+    return CUP_OK;
+}
+
+cup_status laswp(Ctx &c, int64_t row0, int64_t nrows, int64_t k0, int64_t k1)
+{
+    cup_handle *h = c.h;
+    if (nrows <= 0 || k1 <= k0) return CUP_OK;
+    CK(ensure_pairs(h, k1 - k0));
+    CU(launch_swaplist(c.ipiv, k0, k1, h->d_pairs, h->d_count, c.st));
+    CU(launch_laswp(c.A, c.lda, row0, nrows, h->d_pairs, h->d_count, c.st));
+    return CUP_OK;
+}
+
+cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                  const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K, const ModP &Mp,
+                  int engine, cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return CUP_OK;
+    (void)engine;
+    CU(launch_gemm_sub_cc(A, lda, B, ldb, C, ldc, M, N, K, Mp, st));
+    return CUP_OK;
+}
+
+cup_status trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
+                    int64_t m, int64_t n, const ModP &M, int engine, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return CUP_OK;
+    if (n <= 32) {
+        CU(launch_trsm_ruu_leaf(U, ldu, B, ldb, m, (int)n, M, st));
+        return CUP_OK;
+    }
+    // Algorithm 2: B1 <- B1 U1^{-1}; B2 <- B2 - B1 V; B2 <- B2 U2^{-1}
+    int64_t k = ((n / 2) + 31) / 32 * 32;
+    CK(trsm_ruu(h, U, ldu, B, ldb, m, k, M, engine, st));
+    CK(mm_sub(h, B + k, ldb, B, ldb, U + k, ldu, m, n - k, k, M, engine, st));
+    CK(trsm_ruu(h, U + k * ldu + k, ldu, B + k, ldb, m, n - k, M, engine, st));
+    return CUP_OK;
+}
+
+cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_out)
+{
+    cup_handle *h = c.h;
+    const int64_t w = c.n - col0;
+    *r_out = 0;
+    if (w <= 0 || mrows <= 0) return CUP_OK;
+    int64_t k, r1;
+    if (mrows <= h->leaf_rows) {
+        CU(launch_slab_pivots(c.A, c.lda, a, (int)mrows, col0, w, h->window, c.M, h->d_slab,
+                              c.ipiv, c.prof, c.st));
+        CU(cudaMemcpyAsync(h->h_pinned, h->d_slab, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        CU(launch_slab_finish(c.A, c.lda, a, col0, w, c.M, h->d_slab, c.st));
+        CU(cudaStreamSynchronize(c.st));
+        r1 = h->h_pinned[0];
+        k = h->h_pinned[1];
+        if (k == mrows) { *r_out = r1; return CUP_OK; }
+    } else {
+        int64_t nl = (mrows + h->leaf_rows - 1) / h->leaf_rows;
+        k = ((nl + 1) / 2) * h->leaf_rows;
+        CK(cup_rec(c, a, k, col0, &r1));
+    }
+    const int64_t a2 = a + k, m2 = mrows - k;
+    if (r1 > 0) {
+        uint32_t *A = c.A;
+        const int64_t lda = c.lda;
+        CK(laswp(c, a2, m2, col0, col0 + r1));
+        CK(trsm_ruu(h, A + col0 * lda + col0, lda, A + a2 * lda + col0, lda, m2, r1, c.M,
+                    h->engine, c.st));
+        if (col0 + r1 < c.n)
+            CK(mm_sub(h, A + a2 * lda + col0 + r1, lda, A + a2 * lda + col0, lda,
+                      A + col0 * lda + col0 + r1, lda, m2, c.n - col0 - r1, r1, c.M, h->engine,
+                      c.st));
+    }
+    int64_t r2 = 0;
+    CK(cup_rec(c, a2, m2, col0 + r1, &r2));
+    if (r1 > 0 && r2 > 0) CK(laswp(c, col0, r1, col0 + r1, col0 + r1 + r2));
+    *r_out = r1 + r2;
+    return CUP_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+cup_status cup_create(cup_handle **handle, int device)
+{
+    if (!handle) return CUP_ERR_ARG;
+    *handle = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return CUP_ERR_ARG;
+    cup_handle *h = new (std::nothrow) cup_handle();
+    if (!h) return CUP_ERR_NOMEM;
+    h->device = device;
+    *handle = h;
+    return CUP_OK;
+}
+
+cup_status cup_destroy(cup_handle *h)
+{
+    if (!h) return CUP_ERR_ARG;
+    {
+        DeviceGuard g(h->device);
+        if (h->d_slab) cudaFree(h->d_slab);
+        if (h->d_pairs) cudaFree(h->d_pairs);
+        if (h->d_count) cudaFree(h->d_count);
+        if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    }
+    delete h;
+    return CUP_OK;
+}
+
+cup_status cup_set_option(cup_handle *h, int option, int64_t value)
+{
+    if (!h) return CUP_ERR_ARG;
+    switch (option) {
+    case CUP_OPT_ENGINE:
+        if (value != CUP_ENGINE_PLAIN && value != CUP_ENGINE_TENSOR) return CUP_ERR_ARG;
+        h->engine = (int)value;
+        return CUP_OK;
+    case CUP_OPT_LEAF_ROWS:
+        if (value < 1 || value > CUP_BMAX) return CUP_ERR_ARG;
+        h->leaf_rows = (int)value;
+        return CUP_OK;
+    case CUP_OPT_WINDOW:
+        if (value < 1 || value > CUP_WNMAX) return CUP_ERR_ARG;
+        h->window = (int)value;
+        return CUP_OK;
+    case CUP_OPT_TC_MIN_K:
+        if (value < 1) return CUP_ERR_ARG;
+        h->tc_min_k = value;
+        return CUP_OK;
+    case CUP_OPT_VALIDATE:
+        h->validate = value != 0;
+        return CUP_OK;
+    default:
+        return CUP_ERR_ARG;
+    }
+}
+
+const char *cup_last_cuda_error(cup_handle *h)
+{
+    return h ? h->err : "null handle";
+}
+
+cup_status cup_factor(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                      int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!A || !d_profile || !d_ipiv) return CUP_ERR_ARG;
+    if (n >= (int64_t)1 << 31) return CUP_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, (cudaStream_t)stream};
+    int64_t r = 0;
+    CK(cup_rec(c, 0, m, 0, &r));
+    CU(cudaStreamSynchronize(c.st));
+    *rank = r;
+    return CUP_OK;
+}
+
+cup_status cup_rank_profile(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda,
+                            uint32_t p, int64_t *d_profile, int64_t *rank, void *stream)
+{
+    if (!h) return CUP_ERR_ARG;
+    int64_t k = m < n ? m : n;
+    if (k <= 0) return cup_factor(h, A, m, n, lda, p, d_profile, d_profile, rank, stream);
+    int64_t *d_ipiv = nullptr;
+    {
+        DeviceGuard g(h->device);
+        CU(cudaMalloc(&d_ipiv, (size_t)k * sizeof(int64_t)));
+    }
+    cup_status s = cup_factor(h, A, m, n, lda, p, d_profile, d_ipiv, rank, stream);
+    {
+        DeviceGuard g(h->device);
+        cudaFree(d_ipiv);
+    }
+    return s;
+}
+
+cup_status cup_mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                      const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K, uint32_t p,
+                      int engine, void *stream)
+{
+    if (!h || M < 0 || N < 0 || K < 0) return CUP_ERR_ARG;
+    if (engine != CUP_ENGINE_PLAIN && engine != CUP_ENGINE_TENSOR) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (M == 0 || N == 0 || K == 0) return CUP_OK;
+    if (!C || !A || !B || ldc < N || lda < K || ldb < N) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(mm_sub(h, C, ldc, A, lda, B, ldb, M, N, K, make_modp(p), engine, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+cup_status cup_trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
+                        int64_t m, int64_t n, uint32_t p, void *stream)
+{
+    if (!h || m < 0 || n < 0) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!U || !B || ldu < n || ldb < n) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(trsm_ruu(h, U, ldu, B, ldb, m, n, make_modp(p), h->engine, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+cup_status cup_laswp_cols(cup_handle *h, uint32_t *A, int64_t lda, int64_t row0, int64_t nrows,
+                          const int64_t *d_ipiv, int64_t k0, int64_t k1, void *stream)
+{
+    if (!h || row0 < 0 || nrows < 0 || k0 < 0 || k1 < k0) return CUP_ERR_ARG;
+    if (nrows == 0 || k1 == k0) return CUP_OK;
+    if (!A || !d_ipiv || lda < 1) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    Ctx c{h, A, lda, lda, make_modp(2), const_cast<int64_t *>(d_ipiv), nullptr, (cudaStream_t)stream};
+    CK(laswp(c, row0, nrows, k0, k1));
+    return CUP_OK;
+}
+
+cup_status cup_det(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t p, uint32_t *det,
+                   void *stream)
+{
+    if (!h || !det || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (n == 0) { *det = 1u % p; return CUP_OK; }
+    if (!A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    int64_t *d_idx = nullptr;
+    uint32_t *d_out = nullptr;
+    CU(cudaMalloc(&d_idx, 2 * (size_t)n * sizeof(int64_t)));
+    cup_status s = CUP_OK;
+    int64_t r = 0;
+    s = cup_factor(h, A, n, n, lda, p, d_idx, d_idx + n, &r, stream);
+    if (s == CUP_OK) {
+        if (r < n) {
+            *det = 0;
+        } else {
+            s = cuda_ok(h, cudaMalloc(&d_out, sizeof(uint32_t)));
+            if (s == CUP_OK)
+                s = cuda_ok(h, launch_det_reduce(A, lda, n, d_idx + n, make_modp(p), d_out,
+                                                 (cudaStream_t)stream));
+            if (s == CUP_OK)
+                s = cuda_ok(h, cudaMemcpyAsync(h->h_pinned, d_out, sizeof(uint32_t),
+                                               cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+            if (s == CUP_OK) s = cuda_ok(h, cudaStreamSynchronize((cudaStream_t)stream));
+            if (s == CUP_OK) *det = (uint32_t)h->h_pinned[0];
+        }
+    }
+    cudaFree(d_idx);
+    if (d_out) cudaFree(d_out);
+    return s;
+}
+
+cup_status cup_inverse(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t p, void *stream)
+{
+    (void)h; (void)A; (void)n; (void)lda; (void)p; (void)stream;
+    return CUP_ERR_UNSUPPORTED;
+}
+
+cup_status cup_rref(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                    int64_t *d_profile, int64_t *rank, uint32_t *X, int64_t ldx, void *stream)
+{
+    (void)h; (void)A; (void)m; (void)n; (void)lda; (void)p; (void)d_profile; (void)rank; (void)X;
+    (void)ldx; (void)stream;
+    return CUP_ERR_UNSUPPORTED;
+}
+
+cup_status cup_solve(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t *B,
+                     int64_t k, int64_t ldb, uint32_t *X, int64_t ldx, uint32_t p, int64_t *rank,
+                     void *stream)
+{
+    (void)h; (void)A; (void)m; (void)n; (void)lda; (void)B; (void)k; (void)ldb; (void)X; (void)ldx;
+    (void)p; (void)rank; (void)stream;
+    return CUP_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,546 @@
+// CUDA-core kernels of the CUP hot path over GF(p):
+//   * the row-block base case (a slab of at most CUP_BMAX rows), split into a
+//     one-CTA pivot kernel and a grid-wide finish kernel;
+//   * column transpositions (the A2 <- A2 P1^T and V1 <- V1 P2^T steps);
+//   * the TRSM(Right, Upper, Unit) leaf of the recursive triangular solve;
+//   * the CUDA-core INT64 Schur update C <- C - A B mod p (plain path, and the
+//     thin-K fallback of the tensor-core path).
+//
+// The base case generalises the m = 1 case of Algorithm 6 (Sec. 3.3) to a
+// block of rows: rows are taken in order, the pivot of a row is the first
+// nonzero entry of its residual at a position >= the current rank, and that
+// column is transposed with the leading position. The elimination inside the
+// slab is fraction-free (row i' <- f row i' - m row i with f the pivot and m
+// the entry below it), so no field inversion sits on the per-row critical
+// path; the scale factors are products of the pivots and are divided out once
+// at the end with inversions computed in parallel.
+#include <climits>
+#include "cup_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Leaf slab, pivot phase (one CTA).
+//
+// Window: positions [0, wne) of the slab rows [a, a + brows), columns
+// [col0, col0 + w). The window is eliminated eagerly; the columns T of a
+// row-operation matrix (T * slab = eliminated slab) are carried alongside, so
+// that U's rows over the whole width are Minv * (pivot rows of the slab),
+// which the finish kernel evaluates as a small matrix product.
+//
+// A row whose window residual is zero while pivots already exist in this slab
+// cannot be classified without its residual beyond the window: the kernel then
+// stops and reports i_stop; the caller applies the update of the resolved rows
+// to the remaining rows (TRSM + MM, as at an internal node of Algorithm 6) and
+// calls the kernel again on them.
+// ---------------------------------------------------------------------------
+#define PIV_THREADS 256
+#define PIV_LDW (CUP_WNMAX + CUP_BMAX + 1)
+
+__global__ void __launch_bounds__(PIV_THREADS)
+k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, int64_t col0,
+              int64_t w, int wn, ModP M, SlabScratch *__restrict__ S, int64_t *__restrict__ g_ipiv,
+              int64_t *__restrict__ g_prof)
+{
+    extern __shared__ uint32_t W[];            // brows x PIV_LDW: window, then T columns
+    __shared__ int s_wcol[CUP_WNMAX];
+    __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX];
+    __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_Sinv[CUP_BMAX], s_Sfwd[CUP_BMAX];
+    __shared__ int s_c, s_ext;
+
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int wne = (int)(w < (int64_t)wn ? w : (int64_t)wn);
+    const int TC = CUP_WNMAX;
+
+    for (int idx = tid; idx < brows * wne; idx += nt) {
+        int i = idx / wne, q = idx - i * wne;
+        W[i * PIV_LDW + q] = A[(a + i) * lda + col0 + q];
+    }
+    for (int idx = tid; idx < brows * brows; idx += nt) {
+        int i = idx / brows, j = idx - i * brows;
+        W[i * PIV_LDW + TC + j] = 0u;
+    }
+    for (int q = tid; q < wne; q += nt) s_wcol[q] = q;
+    if (tid == 0) s_ext = -1;
+    __syncthreads();
+
+    int r = 0, stop = brows;
+    uint32_t Sprod = 1u % M.p;                 // product of the pivots f taken so far
+    for (int i = 0; i < brows; ++i) {
+        if ((int64_t)r >= w) break;            // every column is a pivot: later rows are dependent
+        if (warp == 0) {
+            int c = -1;
+            for (int q0 = r; q0 < wne; q0 += 32) {
+                int q = q0 + lane;
+                uint32_t v = (q < wne) ? W[i * PIV_LDW + q] : 0u;
+                unsigned bal = __ballot_sync(0xffffffffu, v != 0u);
+                if (bal) { c = q0 + __ffs(bal) - 1; break; }
+            }
+            if (lane == 0) s_c = c;
+        }
+        __syncthreads();
+        int c = s_c;
+        __syncthreads();
+        if (c < 0) {
+            if ((int64_t)wne == w) continue;   // whole residual known and zero
+            if (r != 0) { stop = i; break; }
+            // No pivot yet in this slab: row i of A is still the unreduced,
+            // unpermuted input, so its first nonzero beyond the window is read directly.
+            if (tid == 0) s_c = INT_MAX;
+            __syncthreads();
+            const uint32_t *row = A + (a + i) * lda + col0;
+            for (int64_t q = wne + tid; q < w; q += nt)
+                if (row[q]) { atomicMin(&s_c, (int)q); break; }
+            __syncthreads();
+            c = s_c;
+            __syncthreads();
+            if (c == INT_MAX) continue;        // zero row
+            for (int ii = tid; ii < brows; ii += nt)
+                W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
+            if (tid == 0) { s_ext = c; s_wcol[0] = c; }
+            __syncthreads();
+        } else if (c != r) {
+            for (int ii = tid; ii < brows; ii += nt) {
+                uint32_t x = W[ii * PIV_LDW + r];
+                W[ii * PIV_LDW + r] = W[ii * PIV_LDW + c];
+                W[ii * PIV_LDW + c] = x;
+            }
+            if (tid == 0) { int x = s_wcol[r]; s_wcol[r] = s_wcol[c]; s_wcol[c] = x; }
+            __syncthreads();
+        }
+        const uint32_t f = W[i * PIV_LDW + r];
+        if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
+        // rows below: window positions (r, wne) and T columns [0, i]
+        const int nwin = wne - r - 1;
+        const int ncols = nwin + i + 1;
+        const int nrows = brows - i - 1;
+        for (int idx = tid; idx < nrows * ncols; idx += nt) {
+            int di = idx / ncols, j = idx - di * ncols;
+            int ii = i + 1 + di;
+            uint32_t m = W[ii * PIV_LDW + r];
+            if (j < nwin) {
+                int q = r + 1 + j;
+                W[ii * PIV_LDW + q] = ffupd(f, W[ii * PIV_LDW + q], m, W[i * PIV_LDW + q], M);
+            } else {
+                int jj = j - nwin;             // T column jj <= i; T[i][i] is the product Sprod
+                uint32_t y = (jj == i) ? Sprod : W[i * PIV_LDW + TC + jj];
+                W[ii * PIV_LDW + TC + jj] = ffupd(f, W[ii * PIV_LDW + TC + jj], m, y, M);
+            }
+        }
+        __syncthreads();
+        Sprod = mulm(Sprod, f, M);
+        ++r;
+    }
+    const int rs = r;
+
+    for (int t = tid; t < rs; t += nt) s_finv[t] = invm(s_f[t], M);
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 1u % M.p;
+        for (int t = 0; t < rs; ++t) { s_Sinv[t] = acc; acc = mulm(acc, s_finv[t], M); }
+    }
+    __syncthreads();
+
+    // C values of the resolved rows: W[i][t] carries the scale prod_{t'<t} f_{t'}
+    for (int idx = tid; idx < stop * rs; idx += nt) {
+        int i = idx / rs, t = idx - i * rs;
+        uint32_t v = (i >= s_prof[t]) ? mulm(W[i * PIV_LDW + t], s_Sinv[t], M) : 0u;
+        S->Cn[i][t] = v;
+    }
+    // Minv[t][t'] = T[prof t][prof t'] / f_t, with T's diagonal entry the scale of row prof t
+    for (int idx = tid; idx < rs * rs; idx += nt) {
+        int t = idx / rs, u = idx - t * rs;
+        uint32_t v = 0u;
+        if (u < t) v = mulm(W[s_prof[t] * PIV_LDW + TC + s_prof[u]], s_finv[t], M);
+        else if (u == t) v = mulm(s_Sfwd[t], s_finv[t], M);
+        S->Minv[t][u] = v;
+    }
+    __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 1];
+    if (tid == 0) {
+        int ns = 0;
+        for (int q = 0; q < wne; ++q) {
+            int sl = (s_wcol[q] != q) ? ns++ : -1;
+            S->win_col[q] = s_wcol[q];
+            S->win_slot[q] = sl;
+            if (sl >= 0) s_sorig[sl] = s_wcol[q];
+        }
+        S->ext_pos = s_ext;
+        S->ext_slot = -1;
+        if (s_ext >= 0) { S->ext_slot = ns; s_sorig[ns] = 0; ++ns; }
+        s_slot[0] = ns;
+        S->n_slot = ns;
+        S->r_s = rs;
+        S->i_stop = stop;
+        S->wne = wne;
+    }
+    for (int t = tid; t < rs; t += nt) {
+        S->prof[t] = s_prof[t];
+        g_ipiv[col0 + t] = col0 + s_pos[t];
+        g_prof[col0 + t] = a + s_prof[t];
+    }
+    __syncthreads();
+    // original pivot-row values of every displaced position
+    const int nslot = s_slot[0];
+    for (int idx = tid; idx < nslot * rs; idx += nt) {
+        int sl = idx / rs, t = idx - sl * rs;
+        S->Dorig[sl][t] = A[(a + s_prof[t]) * lda + col0 + s_sorig[sl]];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf slab, finish phase (grid over column positions).
+//
+// For each position q of the slab: U's rows at q are Minv times the original
+// pivot-row values of the column now at q (via the recorded transpositions);
+// the final [C\U] content is then written with U's rows placed directly at
+// global rows col0 .. col0 + r_s (their place in the space-sharing storage of
+// the whole matrix) and C in the slab rows.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int64_t col0, int64_t w, ModP M,
+              const SlabScratch *__restrict__ S)
+{
+    __shared__ uint32_t sMinv[CUP_BMAX][CUP_BMAX + 1];
+    __shared__ uint32_t sX[CUP_BMAX][CUP_QT];
+    __shared__ uint32_t sU[CUP_BMAX][CUP_QT];
+    __shared__ int sOrig[CUP_QT], sSlot[CUP_QT], sProf[CUP_BMAX];
+
+    const int rs = S->r_s, stop = S->i_stop, wne = S->wne;
+    const int64_t q0 = (int64_t)blockIdx.x * CUP_QT;
+    if (q0 >= w) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
+
+    for (int idx = tid; idx < rs * rs; idx += nt) {
+        int t = idx / rs, u = idx - t * rs;
+        sMinv[t][u] = S->Minv[t][u];
+    }
+    for (int t = tid; t < rs; t += nt) sProf[t] = S->prof[t];
+    for (int qq = tid; qq < nq; qq += nt) {
+        int64_t q = q0 + qq;
+        int orig, slot;
+        if (q < wne) { orig = S->win_col[q]; slot = S->win_slot[q]; }
+        else if (q == S->ext_pos) { orig = 0; slot = S->ext_slot; }
+        else { orig = (int)q; slot = -1; }
+        sOrig[qq] = orig;
+        sSlot[qq] = slot;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rs * nq; idx += nt) {
+        int t = idx / nq, qq = idx - t * nq;
+        int slot = sSlot[qq];
+        sX[t][qq] = (slot >= 0) ? S->Dorig[slot][t] : A[(a + sProf[t]) * lda + col0 + sOrig[qq]];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rs * nq; idx += nt) {
+        int t = idx / nq, qq = idx - t * nq;
+        Acc acc = {0ull, 0u};
+        for (int u = 0; u <= t; ++u) acc_add(acc, (uint64_t)sMinv[t][u] * sX[u][qq]);
+        sU[t][qq] = acc_red(acc, M);
+    }
+    __syncthreads();
+    // rows: U rows col0 + t (t < rs), then slab rows a + i (i < stop) that are not U rows
+    const int nrow = rs + stop;
+    for (int idx = tid; idx < nrow * nq; idx += nt) {
+        int k = idx / nq, qq = idx - k * nq;
+        int64_t q = q0 + qq;
+        int64_t rho;
+        uint32_t v;
+        if (k < rs) {
+            rho = col0 + k;
+            if (q > k) v = sU[k][qq];
+            else if (rho >= a) v = (q < rs) ? S->Cn[rho - a][q] : 0u;
+            else v = 0u;
+        } else {
+            int i = k - rs;
+            rho = a + i;
+            if (rho < col0 + rs) continue;     // written above as a U row
+            v = (q < rs) ? S->Cn[i][q] : 0u;
+        }
+        A[rho * lda + col0 + q] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column transpositions. The recorded pivots ipiv[t] (absolute positions) are
+// first compacted to the nontrivial ones, in order; then every row applies
+// them in sequence (Sec. 1.1: right multiplication by P^T permutes columns).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_swaplist(const int64_t *__restrict__ ipiv, int64_t k0, int64_t k1, int2 *__restrict__ pairs,
+           int *__restrict__ count)
+{
+    __shared__ int warp_cnt[32], warp_excl[32];
+    __shared__ int chunk_total, base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base = 0;
+    __syncthreads();
+    for (int64_t c0 = k0; c0 < k1; c0 += 1024) {
+        int64_t t = c0 + tid;
+        int64_t c = (t < k1) ? ipiv[t] : t;
+        bool nz = (t < k1) && (c != t);
+        unsigned bal = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            int v = warp_cnt[lane];
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            warp_excl[lane] = incl - v;
+            if (lane == 31) chunk_total = incl;
+        }
+        __syncthreads();
+        if (nz) {
+            int off = base + warp_excl[warp] + __popc(bal & ((1u << lane) - 1u));
+            pairs[off] = make_int2((int)t, (int)c);
+        }
+        __syncthreads();
+        if (tid == 0) base += chunk_total;
+        __syncthreads();
+    }
+    if (tid == 0) *count = base;
+}
+
+__global__ void __launch_bounds__(256)
+k_laswp(uint32_t *__restrict__ A, int64_t lda, int64_t row0, int64_t nrows,
+        const int2 *__restrict__ pairs, const int *__restrict__ count)
+{
+    __shared__ int2 sp[256];
+    const int n = *count;
+    if (n == 0) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t *row = A + (row0 + i) * lda;
+    for (int b = 0; b < n; b += 256) {
+        __syncthreads();
+        if (b + (int)threadIdx.x < n) sp[threadIdx.x] = pairs[b + threadIdx.x];
+        __syncthreads();
+        if (i < nrows) {
+            int e = (n - b) < 256 ? (n - b) : 256;
+            for (int k = 0; k < e; ++k) {
+                int2 pr = sp[k];
+                uint32_t x = row[pr.x];
+                row[pr.x] = row[pr.y];
+                row[pr.y] = x;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TRSM(Right, Upper, Unit) leaf: B[:, 0:n) <- B[:, 0:n) U^{-1} for an n x n
+// (n <= 32) unit upper block U; one thread per row, forward substitution
+// x_j = b_j - sum_{k<j} x_k u_kj (Algorithm 2 at its base, unit diagonal).
+// ---------------------------------------------------------------------------
+#define TRSM_LEAF 32
+__global__ void __launch_bounds__(128)
+k_trsm_ruu_leaf(const uint32_t *__restrict__ U, int64_t ldu, uint32_t *__restrict__ B, int64_t ldb,
+                int64_t m, int n, ModP M)
+{
+    __shared__ uint32_t sU[TRSM_LEAF][TRSM_LEAF + 1];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        int k = idx / n, j = idx - k * n;
+        sU[k][j] = (j > k) ? U[k * ldu + j] : 0u;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t *row = B + i * ldb;
+    uint32_t x[TRSM_LEAF];
+#pragma unroll
+    for (int j = 0; j < TRSM_LEAF; ++j) x[j] = (j < n) ? row[j] : 0u;
+#pragma unroll
+    for (int j = 1; j < TRSM_LEAF; ++j) {
+        Acc acc = {0ull, 0u};
+#pragma unroll
+        for (int k = 0; k < j; ++k) acc_add(acc, (uint64_t)x[k] * sU[k][j]);
+        x[j] = subm(x[j], acc_red(acc, M), M);
+    }
+#pragma unroll
+    for (int j = 0; j < TRSM_LEAF; ++j)
+        if (j < n) row[j] = x[j];
+}
+
+// ---------------------------------------------------------------------------
+// Plain CUDA-core Schur update C <- C - A B mod p (Algorithm 1, alpha = -1,
+// beta = 1). 64 x 64 tiles, 4 x 4 outputs per thread, exact 64-bit products;
+// when K (p-1)^2 may reach 2^64 the accumulators also count wraps.
+// ---------------------------------------------------------------------------
+#define GB_M 64
+#define GB_N 64
+#define GB_K 16
+template <bool WIDE>
+__global__ void __launch_bounds__(256)
+k_gemm_sub_cc(const uint32_t *__restrict__ A, int64_t lda, const uint32_t *__restrict__ B,
+              int64_t ldb, uint32_t *__restrict__ C, int64_t ldc, int64_t Mr, int64_t N, int64_t K,
+              ModP Mp)
+{
+    __shared__ uint32_t As[GB_K][GB_M + 4];
+    __shared__ uint32_t Bs[GB_K][GB_N + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * GB_M, n0 = (int64_t)blockIdx.x * GB_N;
+    uint64_t acc[4][4];
+    uint32_t hi[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { acc[i][j] = 0ull; hi[i][j] = 0u; }
+
+    for (int64_t k0 = 0; k0 < K; k0 += GB_K) {
+        for (int idx = threadIdx.x; idx < GB_M * GB_K; idx += 256) {
+            int r = idx / GB_K, kk = idx - r * GB_K;
+            int64_t gr = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gr < Mr && gk < K) ? A[gr * lda + gk] : 0u;
+        }
+        for (int idx = threadIdx.x; idx < GB_K * GB_N; idx += 256) {
+            int kk = idx / GB_N, c = idx - kk * GB_N;
+            int64_t gk = k0 + kk, gc = n0 + c;
+            Bs[kk][c] = (gk < K && gc < N) ? B[gk * ldb + gc] : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            uint32_t av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint64_t pr = (uint64_t)av[i] * bv[j];
+                    if (WIDE) {
+                        uint64_t s = acc[i][j] + pr;
+                        hi[i][j] += (s < pr);
+                        acc[i][j] = s;
+                    } else {
+                        acc[i][j] += pr;
+                    }
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t gr = m0 + ty + 16 * i, gc = n0 + tx + 16 * j;
+            if (gr < Mr && gc < N) {
+                Acc a = {acc[i][j], hi[i][j]};
+                uint32_t v = acc_red(a, Mp);
+                uint32_t *cp = C + gr * ldc + gc;
+                *cp = subm(*cp, v, Mp);
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, int64_t col0,
+                               int64_t w, int wn, ModP M, SlabScratch *S, int64_t *ipiv,
+                               int64_t *prof, cudaStream_t st)
+{
+    static bool attr = false;
+    size_t smem = (size_t)brows * PIV_LDW * sizeof(uint32_t);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_slab_pivots, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(CUP_BMAX * PIV_LDW * sizeof(uint32_t)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_slab_pivots<<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, w, wn, M, S, ipiv, prof);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int64_t col0, int64_t w,
+                               ModP M, const SlabScratch *S, cudaStream_t st)
+{
+    int64_t nb = (w + CUP_QT - 1) / CUP_QT;
+    if (nb <= 0) return cudaSuccess;
+    k_slab_finish<<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, w, M, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_swaplist(const int64_t *ipiv, int64_t k0, int64_t k1, int2 *pairs, int *count,
+                            cudaStream_t st)
+{
+    k_swaplist<<<1, 1024, 0, st>>>(ipiv, k0, k1, pairs, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_laswp(uint32_t *A, int64_t lda, int64_t row0, int64_t nrows, const int2 *pairs,
+                         const int *count, cudaStream_t st)
+{
+    if (nrows <= 0) return cudaSuccess;
+    int64_t nb = (nrows + 255) / 256;
+    k_laswp<<<(unsigned)nb, 256, 0, st>>>(A, lda, row0, nrows, pairs, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
+                                 int64_t m, int n, ModP M, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m + 127) / 128;
+    k_trsm_ruu_leaf<<<(unsigned)nb, 128, 0, st>>>(U, ldu, B, ldb, m, n, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
+                               uint32_t *C, int64_t ldc, int64_t Mr, int64_t N, int64_t K, ModP M,
+                               cudaStream_t st)
+{
+    if (Mr <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((N + GB_N - 1) / GB_N), (unsigned)((Mr + GB_M - 1) / GB_M));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    // K (p-1)^2 < 2^64 means the 64-bit sum of products cannot wrap
+    long double bound = (long double)K * (long double)(M.p - 1) * (long double)(M.p - 1);
+    if (bound < 18446744073709551615.0L)
+        k_gemm_sub_cc<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M);
+    else
+        k_gemm_sub_cc<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Determinant from a full-rank CUP: the product of C's diagonal (the pivots,
+// stored on A's diagonal by [C\U]) times (-1)^(number of nontrivial
+// transpositions) (Sec. 5; for rank n the profile is 0..n-1, so pivot t sits
+// at (t, t)). One CTA, tree product modulo p.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_det_reduce(const uint32_t *__restrict__ A, int64_t lda, int64_t n, const int64_t *__restrict__ ipiv,
+             ModP M, uint32_t *__restrict__ out)
+{
+    __shared__ uint32_t sp[1024];
+    __shared__ int sneg[1024];
+    uint32_t prod = 1u % M.p;
+    int neg = 0;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        prod = mulm(prod, A[t * lda + t], M);
+        neg ^= (ipiv[t] != t);
+    }
+    sp[threadIdx.x] = prod;
+    sneg[threadIdx.x] = neg;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sp[threadIdx.x] = mulm(sp[threadIdx.x], sp[threadIdx.x + s], M);
+            sneg[threadIdx.x] ^= sneg[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        uint32_t d = sp[0];
+        *out = (sneg[0] && d) ? M.p - d : d;
+    }
+}
+
+cudaError_t launch_det_reduce(const uint32_t *A, int64_t lda, int64_t n, const int64_t *ipiv, ModP M,
+                              uint32_t *out, cudaStream_t st)
+{
+    k_det_reduce<<<1, 1024, 0, st>>>(A, lda, n, ipiv, M, out);
+    return cudaGetLastError();
+}
