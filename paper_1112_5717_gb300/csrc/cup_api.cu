@@ -24,7 +24,7 @@
 
 struct cup_handle {
     int device = 0;
-    int engine = CUP_ENGINE_PLAIN;
+    int engine = CUP_ENGINE_TENSOR;
     int leaf_rows = 32;
     int window = 64;
     int64_t tc_min_k = 256;
@@ -34,6 +34,9 @@ struct cup_handle {
     int64_t pairs_cap = 0;
     int *d_count = nullptr;
     int *h_pinned = nullptr;
+    int *d_err = nullptr;          // device-side error word of the tensor-core kernels
+    void *d_ws = nullptr;          // limb planes of the tensor-core Schur update
+    size_t ws_bytes = 0;
     char err[256] = {0};
 };
 
@@ -119,6 +122,35 @@ cup_status ensure_base(cup_handle *h)
     if (!h->d_slab) CU(cudaMalloc(&h->d_slab, sizeof(SlabScratch)));
     if (!h->d_count) CU(cudaMalloc(&h->d_count, sizeof(int)));
     if (!h->h_pinned) CU(cudaMallocHost(&h->h_pinned, 16 * sizeof(int)));
+    if (!h->d_err) {
+        CU(cudaMalloc(&h->d_err, sizeof(int)));
+        CU(cudaMemset(h->d_err, 0, sizeof(int)));
+    }
+    return CUP_OK;
+}
+
+cup_status ensure_ws(cup_handle *h, size_t bytes)
+{
+    if (bytes <= h->ws_bytes) return CUP_OK;
+    if (h->d_ws) cudaFree(h->d_ws);
+    h->d_ws = nullptr;
+    h->ws_bytes = 0;
+    CU(cudaMalloc(&h->d_ws, bytes));
+    h->ws_bytes = bytes;
+    return CUP_OK;
+}
+
+// Reads the device error word after `st` drains; a set word means a bounded
+// device-side wait gave up.
+cup_status check_device_error(cup_handle *h, cudaStream_t st)
+{
+    CU(cudaMemcpyAsync(h->h_pinned + 8, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h->h_pinned[8] != 0) {
+        snprintf(h->err, sizeof(h->err), "device wait expired (site %d)", h->h_pinned[8]);
+        cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
+        return CUP_ERR_TIMEOUT;
+    }
     return CUP_OK;
 }
 
@@ -137,7 +169,12 @@ cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, in
                   int engine, cudaStream_t st)
 {
     if (M <= 0 || N <= 0 || K <= 0) return CUP_OK;
-    (void)engine;
+    if (engine == CUP_ENGINE_TENSOR && K >= h->tc_min_k) {
+        CK(ensure_base(h));
+        CK(ensure_ws(h, tc_workspace_bytes(Mp.p, M, N, K)));
+        CU(launch_gemm_sub_tc(A, lda, B, ldb, C, ldc, M, N, K, Mp, h->d_ws, h->d_err, st));
+        return CUP_OK;
+    }
     CU(launch_gemm_sub_cc(A, lda, B, ldb, C, ldc, M, N, K, Mp, st));
     return CUP_OK;
 }
@@ -239,6 +276,8 @@ cup_status cup_destroy(cup_handle *h)
         if (h->d_pairs) cudaFree(h->d_pairs);
         if (h->d_count) cudaFree(h->d_count);
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
+        if (h->d_err) cudaFree(h->d_err);
+        if (h->d_ws) cudaFree(h->d_ws);
     }
     delete h;
     return CUP_OK;
@@ -291,7 +330,7 @@ cup_status cup_factor(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t 
     Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, (cudaStream_t)stream};
     int64_t r = 0;
     CK(cup_rec(c, 0, m, 0, &r));
-    CU(cudaStreamSynchronize(c.st));
+    CK(check_device_error(h, c.st));
     *rank = r;
     return CUP_OK;
 }
@@ -325,7 +364,9 @@ cup_status cup_mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A
     if (M == 0 || N == 0 || K == 0) return CUP_OK;
     if (!C || !A || !B || ldc < N || lda < K || ldb < N) return CUP_ERR_ARG;
     DeviceGuard g(h->device);
+    CK(ensure_base(h));
     CK(mm_sub(h, C, ldc, A, lda, B, ldb, M, N, K, make_modp(p), engine, (cudaStream_t)stream));
+    CK(check_device_error(h, (cudaStream_t)stream));
     return CUP_OK;
 }
 
@@ -337,7 +378,9 @@ cup_status cup_trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t 
     if (m == 0 || n == 0) return CUP_OK;
     if (!U || !B || ldu < n || ldb < n) return CUP_ERR_ARG;
     DeviceGuard g(h->device);
+    CK(ensure_base(h));
     CK(trsm_ruu(h, U, ldu, B, ldb, m, n, make_modp(p), h->engine, (cudaStream_t)stream));
+    CK(check_device_error(h, (cudaStream_t)stream));
     return CUP_OK;
 }
 

@@ -43,3 +43,10 @@ cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B
                                cudaStream_t st);
 cudaError_t launch_det_reduce(const uint32_t *A, int64_t lda, int64_t n, const int64_t *ipiv, ModP M,
                               uint32_t *out, cudaStream_t st);
+
+// Tensor-core Schur update (cup_tc.cu).
+int tc_limbs(uint32_t p);
+size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K);
+cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
+                               int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
+                               cudaStream_t st);

@@ -1,2 +1,492 @@
-// tcgen05 tensor-core Schur update on exact 8-bit limbs (placeholder unit).
+// Tensor-core Schur update over GF(p): C <- C - A B mod p (Algorithm 1 with
+// alpha = -1, beta = 1, the MM step of Algorithm 6 and of Algorithm 2's TRSM).
+//
+// Exact integer products on tcgen05 (sm_103a has no integer tcgen05 kind):
+//   * every residue x in [0, p) is centred (x - p when x > (p-1)/2) and split
+//     into L signed base-256 digits d_l in [-128, 128] (L = 1, 2, 3, 4 for
+//     p below 2^8, 2^16, 2^24, 2^31); |d| <= 256 is exact in bf16;
+//   * limb products are accumulated by tcgen05.mma kind::f16 (bf16 in,
+//     fp32 accumulate in TMEM), one accumulator D_s per digit shift s = i + j,
+//     D_s = sum_{i+j=s} A_i B_j^T. Every term is at most 2^14 in magnitude and
+//     a shift collects at most L products per k, so a chunk of kc values of k
+//     with L * kc * 2^14 <= 2^24 keeps every partial sum an exact fp32
+//     integer;
+//   * after each chunk the epilogue warps read the accumulators from TMEM,
+//     recombine sum_s D_s 256^s in 64-bit integers, reduce mod p and add to a
+//     running residue per output; the last chunk's result is subtracted from C.
+// Operands reach shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle)
+// from limb planes written by the split kernels below.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include "cup_internal.cuh"
+
+namespace tc {
+
+constexpr int BM = 128;       // rows per tile (tcgen05 M)
+constexpr int BK = 64;        // k per pipeline stage: one 128-byte swizzle row of bf16
+constexpr int NEPI = 8;       // epilogue warps (two per TMEM lane quarter)
+constexpr int NTHREADS = 32 * (2 + NEPI);
+constexpr int SMEM_BUDGET = 200 * 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up after ~2 s of wall time and records the failure.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0u) {
+            if (*(volatile int *)err != 0) return false;
+            if (globaltimer() - t0 > 2000000000ull) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of tcgen05 for a K-major operand in the
+// 128-byte swizzled layout TMA writes: 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: bf16 A and B, fp32 D,
+// both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int L>
+struct Cfg {
+    static constexpr int NACC = 2 * L - 1;
+    static constexpr int BN = (NACC * 128 <= 512) ? 128 : 64;
+    static constexpr int STAGE_A = BM * BK * 2;
+    static constexpr int STAGE_B = BN * BK * 2;
+    static constexpr int STAGE = L * (STAGE_A + STAGE_B);
+    static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 8 ? (SMEM_BUDGET / STAGE) : 8;
+    static constexpr int SMEM = NSTAGE * STAGE + 1024;
+    static constexpr int KCHUNK = (1024 / L) / BK * BK;      // L * kc * 2^14 <= 2^24
+    static constexpr int COLS_PER_WARP = BN / 2;
+};
+
+// C[M x N] -= A B (mod p) from limb planes: Al is (L, M, Kp), Bl is (L, N, Kp), bf16, K-major.
+template <int L>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            uint32_t *__restrict__ C, int64_t ldc, int M, int N, int Kp, ModP Mp, uint64_t off,
+            uint32_t sh32, int *__restrict__ err)
+{
+    using CF = Cfg<L>;
+    constexpr int BN = CF::BN, NACC = CF::NACC, NSTAGE = CF::NSTAGE;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], accf_bar, acce_bar;
+    __shared__ uint32_t tmem_base_sh;
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nkb = Kp / BK;
+    const int kb_chunk = CF::KCHUNK / BK;
+    const int nchunk = (nkb + kb_chunk - 1) / kb_chunk;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&accf_bar), 1);
+        mbar_init(smem_u32(&acce_bar), NEPI);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % NSTAGE;
+                const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
+                if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, 1)) break;
+                const uint32_t fb = smem_u32(&full_bar[s]);
+                mbar_expect_tx(fb, CF::STAGE);
+                const uint32_t st = sbase + s * CF::STAGE;
+#pragma unroll
+                for (int l = 0; l < L; ++l) tma_load_3d(st + l * CF::STAGE_A, &tmA, kb * BK, m0, l, fb);
+#pragma unroll
+                for (int l = 0; l < L; ++l)
+                    tma_load_3d(st + L * CF::STAGE_A + l * CF::STAGE_B, &tmB, kb * BK, n0, l, fb);
+                ++issued;
+            }
+            // before leaving, let every issued copy land (bounded)
+            for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
+                mbar_wait(smem_u32(&full_bar[kb % NSTAGE]), (uint32_t)(kb / NSTAGE) & 1u, err, 2);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BN);
+            int kb = 0;
+            bool ok = true;
+            for (int c = 0; c < nchunk && ok; ++c) {
+                if (c > 0 && !mbar_wait(smem_u32(&acce_bar), (uint32_t)(c - 1) & 1u, err, 3)) { ok = false; break; }
+                tc_fence_after();
+                const int kb_first = kb;
+                const int kb_end = (kb + kb_chunk < nkb) ? kb + kb_chunk : nkb;
+                for (; kb < kb_end; ++kb) {
+                    const int s = kb % NSTAGE;
+                    const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
+                    if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, 4)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t st = sbase + s * CF::STAGE;
+#pragma unroll
+                    for (int i = 0; i < L; ++i)
+#pragma unroll
+                        for (int j = 0; j < L; ++j) {
+                            const int sh = i + j;
+                            const int ifirst = sh - (L - 1) > 0 ? sh - (L - 1) : 0;
+                            const uint32_t a_addr = st + i * CF::STAGE_A;
+                            const uint32_t b_addr = st + L * CF::STAGE_A + j * CF::STAGE_B;
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                const uint32_t acc = (kb == kb_first && i == ifirst && kk == 0) ? 0u : 1u;
+                                mma_bf16(tmem + sh * BN, sw128_desc(a_addr + kk * 32),
+                                         sw128_desc(b_addr + kk * 32), idesc, acc);
+                            }
+                        }
+                    mma_commit(smem_u32(&empty_bar[s]));
+                }
+                if (ok) mma_commit(smem_u32(&accf_bar));
+            }
+        }
+    } else {
+        // ---------------- epilogue warps ----------------
+        const int q = warp & 3;                           // TMEM lane quarter this warp may access
+        const int hcol = (warp - 2) >> 2;                 // which half of the BN columns
+        const int row = m0 + 32 * q + lane;
+        constexpr int CPW = CF::COLS_PER_WARP;
+        uint32_t run[CPW];
+#pragma unroll
+        for (int e = 0; e < CPW; ++e) run[e] = 0u;
+        bool ok = true;
+        for (int c = 0; c < nchunk; ++c) {
+            if (!mbar_wait(smem_u32(&accf_bar), (uint32_t)c & 1u, err, 5)) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int cb = 0; cb < CPW / 16; ++cb) {
+                const int col = hcol * CPW + cb * 16;
+                const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col;
+                float d[NACC][16];
+#pragma unroll
+                for (int s = 0; s < NACC; ++s) tmem_ld16(tbase + s * BN, d[s]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    uint32_t r;
+                    if (L <= 3) {
+                        int64_t v = 0;
+#pragma unroll
+                        for (int s = NACC - 1; s >= 0; --s) v = v * 256 + (int64_t)__float2int_rn(d[s][e]);
+                        r = red64((uint64_t)(v + (int64_t)off), Mp);
+                    } else {
+                        int64_t lo = 0, hi = 0;
+#pragma unroll
+                        for (int s = 3; s >= 0; --s) lo = lo * 256 + (int64_t)__float2int_rn(d[s][e]);
+#pragma unroll
+                        for (int s = NACC - 1; s >= 4; --s) hi = hi * 256 + (int64_t)__float2int_rn(d[s][e]);
+                        uint32_t rl = red64((uint64_t)(lo + (int64_t)off), Mp);
+                        uint32_t rh = red64((uint64_t)(hi + (int64_t)off), Mp);
+                        r = red64((uint64_t)rh * sh32 + rl, Mp);
+                    }
+                    run[cb * 16 + e] = addm(run[cb * 16 + e], r, Mp);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce_bar));
+        }
+        if (ok && row < M) {
+            uint32_t *crow = C + (int64_t)row * ldc;
+#pragma unroll
+            for (int e = 0; e < CPW; ++e) {
+                const int gc = n0 + hcol * CPW + e;
+                if (gc < N) crow[gc] = subm(crow[gc], run[e], Mp);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Limb split: residues -> L planes of centred signed base-256 digits in bf16.
+// A (M x K, lda) -> Al[l][i][k], Kp columns (zero padded); B (K x N, ldb) ->
+// Bl[l][j][k] (transposed, K-major).
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void split_digits(uint32_t x, uint32_t p, uint32_t half, __nv_bfloat16 (&d)[L])
+{
+    int32_t v = (x > half) ? (int32_t)(x - p) : (int32_t)x;
+#pragma unroll
+    for (int l = 0; l < L - 1; ++l) {
+        int32_t dl = ((v + 128) & 255) - 128;
+        d[l] = __int2bfloat16_rn(dl);
+        v = (v - dl) >> 8;
+    }
+    d[L - 1] = __int2bfloat16_rn(v);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256)
+k_split_rows(const uint32_t *__restrict__ A, int64_t lda, int M, int K, int Kp, uint32_t p,
+             __nv_bfloat16 *__restrict__ out)
+{
+    // one thread: 8 consecutive k of one row
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int kv = Kp / 8;
+    const int64_t i = idx / kv;
+    const int k0 = (int)(idx - i * kv) * 8;
+    if (i >= M) return;
+    const uint32_t half = (p - 1) / 2;
+    __align__(16) __nv_bfloat16 buf[L][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        __nv_bfloat16 d[L];
+        split_digits<L>(k < K ? A[i * lda + k] : 0u, p, half, d);
+#pragma unroll
+        for (int l = 0; l < L; ++l) buf[l][e] = d[l];
+    }
+    const int64_t plane = (int64_t)M * Kp;
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        *(uint4 *)(out + l * plane + i * Kp + k0) = *(const uint4 *)buf[l];
+}
+
+// B (K x N) -> planes (L, N, Kp): 32 x 32 tiles through shared memory.
+template <int L>
+__global__ void __launch_bounds__(256)
+k_split_cols(const uint32_t *__restrict__ B, int64_t ldb, int K, int N, int Kp, uint32_t p,
+             __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ uint32_t t[32][33];
+    const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
+    for (int r = ty; r < 32; r += 8) {
+        const int k = k0 + r, n = n0 + tx;
+        t[r][tx] = (k < K && n < N) ? B[(int64_t)k * ldb + n] : 0u;
+    }
+    __syncthreads();
+    const uint32_t half = (p - 1) / 2;
+    const int64_t plane = (int64_t)N * Kp;
+    for (int r = ty; r < 32; r += 8) {
+        const int n = n0 + r, k = k0 + tx;
+        if (n < N && k < Kp) {
+            __nv_bfloat16 d[L];
+            split_digits<L>(t[tx][r], p, half, d);
+#pragma unroll
+            for (int l = 0; l < L; ++l) out[l * plane + (int64_t)n * Kp + k] = d[l];
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, void *base, int kp, int rows, int L, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)L};
+    cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * (cuuint64_t)rows};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int L>
+cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C, int64_t ldc,
+                int M, int N, int K, ModP Mp, void *ws, int *err, cudaStream_t st)
+{
+    using CF = Cfg<L>;
+    const int Kp = (K + BK - 1) / BK * BK;
+    __nv_bfloat16 *Al = (__nv_bfloat16 *)ws;
+    __nv_bfloat16 *Bl = Al + (size_t)L * M * Kp;
+    {
+        int64_t nthr = (int64_t)M * (Kp / 8);
+        k_split_rows<L><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(A, lda, M, K, Kp, Mp.p, Al);
+        dim3 g((N + 31) / 32, (Kp + 31) / 32);
+        k_split_cols<L><<<g, 256, 0, st>>>(B, ldb, K, N, Kp, Mp.p, Bl);
+    }
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, Al, Kp, M, L, BM) || !make_map(&tb, Bl, Kp, N, L, CF::BN))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_limb_gemm<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    // offset making the recombined chunk value nonnegative: a multiple of p above its bound
+    const int bound_bits = (L <= 3) ? 60 : 52;
+    const uint64_t off = ((1ull << bound_bits) / Mp.p + 1) * Mp.p;
+    const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
+    dim3 grid((N + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
+    k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, C, ldc, M, N, Kp, Mp, off, sh32, err);
+    return cudaGetLastError();
+}
+
+}  // namespace tc
+
+int tc_limbs(uint32_t p)
+{
+    if (p < (1u << 8)) return 1;
+    if (p < (1u << 16)) return 2;
+    if (p < (1u << 24)) return 3;
+    return 4;
+}
+
+size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K)
+{
+    const int L = tc_limbs(p);
+    const int64_t Kp = (K + tc::BK - 1) / tc::BK * tc::BK;
+    return (size_t)L * (size_t)(M + N) * (size_t)Kp * 2;
+}
+
+cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
+                               int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
+                               cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2) return cudaErrorInvalidValue;
+    switch (tc_limbs(Mp.p)) {
+    case 1: return tc::run<1>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
+    case 2: return tc::run<2>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
+    case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
+    default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
+    }
+}

@@ -129,3 +129,11 @@ def test_det(cuda_lib, n, p):
         want = oracle.det(A, p)
         got = cuda_lib.Handle(engine=0).det(_dev(A), p)
         assert got == want
+
+
+@pytest.mark.parametrize("name", ["dense_plain_512", "rank_def_700x256", "wide_90x500_p2",
+                                  "tall_500x90_p3", "p31", "dense_full_300"])
+@pytest.mark.parametrize("tc_min_k", [1, 64])
+def test_factor_tensor_engine(cuda_lib, name, tc_min_k):
+    A, p = FACTOR_CASES[name]()
+    _factor_case(cuda_lib, A, p, engine=1, tc_min_k=tc_min_k)
