@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 CUP library.
+
+Workload: CUP decomposition (Algorithm 6) of a dense 8192 x 8192 matrix of
+uniform residues over GF(65521), uint32 storage, with the Schur updates on
+tcgen05 tensor cores (2 centred 8-bit limbs per residue). One step is one
+complete in-place factorisation of that matrix; before every step the
+pristine input is restored by a device-to-device copy outside the step's
+events (the 256 MiB input is also larger than the 129 MiB L2).
+
+Metric: field operations per second normalised by the paper's leading-term
+count 2mnr - (m+n)r^2 + 2/3 r^3 (Sec. 4.2), in Gop/s.
+
+  python bench.py [--gpus N --steps K --warmup W]      # our CUDA path
+  python bench.py --impl reference ...                   # the CPU oracle, timed on the host
+
+Under torchrun (N > 1) every rank factors its own replica (one CUP does not
+shard: its pivot search is sequential down the rows); the value is the
+operations of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+METRIC = "CUP GF(p) Gop/s (leading-term normalised)"
+UNIT = "Gop/s"
+
+
+def cup_ops(m: int, n: int, r: int) -> float:
+    """2mnr - (m+n) r^2 + 2/3 r^3: field operations of CUP with classical products (Sec. 4.2)."""
+    return 2.0 * m * n * r - (m + n) * float(r) * r + 2.0 / 3.0 * float(r) ** 3
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--p", type=int, default=65521)
+    ap.add_argument("--engine", choices=["tensor", "plain"], default="tensor")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-engine comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-sample", type=int, default=2048, help="side of the oracle's sample matrix")
+    ap.add_argument("--leaf-rows", type=int, default=None)
+    ap.add_argument("--window", type=int, default=None)
+    ap.add_argument("--tc-min-k", type=int, default=None)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only warm-up and timed factorisations (for profiler launch lists)")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (also exercised by CPU tests with the gloo backend)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        # samples under load: the top half of the clock readings
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle as baseline (test infrastructure, timed as it stands)
+# ---------------------------------------------------------------------------
+def oracle_sample(n: int, p: int):
+    import oracle
+    from paper_1112_5717_gb300 import inputs
+    A = inputs.dense_full(n=n, p=p, seed=inputs.SEED_BASE + 2)
+    t0 = time.perf_counter()
+    d = oracle.cup(A, p)
+    dt = time.perf_counter() - t0
+    return cup_ops(n, n, d["rank"]) / dt / 1e9, dt, oracle.num_threads(), d["rank"]
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n = args.cpu_sample
+    for _ in range(args.warmup):
+        oracle_sample(n, args.p)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, cores, r = oracle_sample(n, args.p)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.median(vals)
+    sample = (f"CUP of one {n}x{n} uniform matrix over GF({args.p}) per step (the {args.n}x{args.n} "
+              f"workload scaled down), leading-term ops / wall time")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(times) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic",
+           "config": {"workload": f"dense_full {args.n}x{args.n} GF({args.p}) CUP (sampled at {n}x{n} on the host)",
+                      "n": n, "p": args.p},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1112_5717_gb300 as cup
+    from paper_1112_5717_gb300 import inputs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    n, p = args.n, args.p
+    engine = cup.ENGINE_TENSOR if args.engine == "tensor" else cup.ENGINE_PLAIN
+
+    A_np = inputs.dense_full(n=n, p=p, seed=inputs.SEED_BASE + 2)
+    A_host = torch.from_numpy(A_np.view(np.int32)).pin_memory()
+    A0 = A_host.to(dev)
+    A = torch.empty_like(A0)
+    opts = {k: v for k, v in (("leaf_rows", args.leaf_rows), ("window", args.window),
+                              ("tc_min_k", args.tc_min_k)) if v is not None}
+    h = cup.Handle(dev, engine=engine, profile=1, **opts)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        A.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r, prof, ipiv = h.factor(A, p)
+        e1.record(stream)
+        return r, e0, e1
+
+    for _ in range(args.warmup):
+        r, _, _ = one_step()
+    torch.cuda.synchronize()
+    rank_val = r
+    h.reset_stats()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        r, e0, e1 = one_step()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    st = h.stats()
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    ops = cup_ops(n, n, rank_val)
+    value = ops * world / (ms_max * 1e-3) / 1e9
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+              "config": {"workload": f"dense_full {n}x{n} uniform over GF({p}), uint32, in-place CUP "
+                                     f"(Algorithm 6) with {args.engine} Schur updates",
+                         "n": n, "p": p, "rank": rank_val, "engine": args.engine,
+                         "limbs": cup_limbs(p) if engine == cup.ENGINE_TENSOR else None,
+                         "l2": "256 MiB input > 129 MiB L2; restored by a device copy before each step",
+                         "parallelism": "replicas" if world > 1 else "single",
+                         "options": opts,
+                         "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
+              "gpu_launches": int(st["launches"]),
+              "clocks": clk}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if st["tc_launches"] and st["tc_ms"] > 0:
+        achieved = st["tc_limb_flops"] / (st["tc_ms"] * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops")
+        src = "measured burst bf16 (MEASURED_PEAKS.json)"
+        if peak is None:
+            peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16"
+        result["roofline"] = {"bound": "tensor", "kernel": "k_limb_gemm", "achieved": achieved, "peak": peak,
+                              "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                              "peak_source": src,
+                              "per_launch_ms": st["tc_ms"] / st["tc_launches"],
+                              "launches": st["tc_launches"],
+                              "field_tops": st["tc_field_flops"] / (st["tc_ms"] * 1e-3) / 1e12,
+                              "share_of_step": st["tc_ms"] / sum(step_ms)}
+    elif st["cc_launches"] and st["cc_ms"] > 0:
+        result["roofline"] = {"bound": "alu", "kernel": "k_gemm_sub_cc",
+                              "achieved": st["cc_field_flops"] / (st["cc_ms"] * 1e-3) / 1e12,
+                              "peak": None, "unit": "Tfield-op/s", "frac": None, "traffic": None}
+    result["stats"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
+
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps(result), flush=True)
+        return 0
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        out_host = torch.empty_like(A_host).pin_memory()
+        e2e_ms = []
+        for i in range(max(args.steps, 1) + 1):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.copy_(A_host, non_blocking=True)
+            r, prof, ipiv = h.factor(A, p)
+            out_host.copy_(A, non_blocking=True)
+            prof_h = prof.to("cpu", non_blocking=True)
+            ipiv_h = ipiv.to("cpu", non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+        e_ms = max_over_ranks(statistics.mean(e2e_ms), world)
+        result["e2e"] = {"value": ops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
+                         "h2d_bytes_per_step": int(A_host.numel() * 4),
+                         "d2h_bytes_per_step": int(out_host.numel() * 4 + prof_h.numel() * 8 + ipiv_h.numel() * 8)}
+
+    # the plain CUDA-core INT64 engine on the same workload
+    if not args.no_plain and engine == cup.ENGINE_TENSOR and world == 1:
+        hp = cup.Handle(dev, engine=cup.ENGINE_PLAIN)
+        A.copy_(A0)
+        hp.factor(A, p)
+        pm = []
+        for _ in range(2):
+            A.copy_(A0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hp.factor(A, p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pm.append(e0.elapsed_time(e1))
+        pms = statistics.mean(pm)
+        result["plain"] = {"value": ops / (pms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pms,
+                           "tensor_over_plain": (ops / (ms * 1e-3) / 1e9) / (ops / (pms * 1e-3) / 1e9)}
+        hp.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, cores, _ = oracle_sample(args.cpu_sample, p)
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": f"CUP of one {args.cpu_sample}x{args.cpu_sample} uniform matrix over "
+                                            f"GF({p}) ({dt:.1f} s), leading-term ops / wall time"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def cup_limbs(p: int) -> int:
+    return 1 if p < 2 ** 8 else 2 if p < 2 ** 16 else 3 if p < 2 ** 24 else 4
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    if args.impl == "reference":
+        return run_reference(args)
+    import paper_1112_5717_gb300.build as b
+    b.build()
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -59,11 +59,28 @@ enum {
 /* Options for cup_set_option. */
 enum {
     CUP_OPT_ENGINE = 0,        /* CUP_ENGINE_PLAIN or CUP_ENGINE_TENSOR (default TENSOR) */
-    CUP_OPT_LEAF_ROWS = 1,     /* rows of a base-case slab, 1..64 (default 32) */
+    CUP_OPT_LEAF_ROWS = 1,     /* rows of a base-case slab, 1..64 (default 64) */
     CUP_OPT_WINDOW = 2,        /* pivot-search window of the base case, 1..128 (default 64) */
-    CUP_OPT_TC_MIN_K = 3,      /* smallest inner dimension sent to the tensor engine */
-    CUP_OPT_VALIDATE = 4       /* nonzero: check inputs are canonical residues (slow) */
+    CUP_OPT_TC_MIN_K = 3,      /* smallest inner dimension sent to the tensor engine (default 64) */
+    CUP_OPT_VALIDATE = 4,      /* nonzero: check inputs are canonical residues (slow) */
+    CUP_OPT_PROFILE = 5        /* nonzero: time every Schur-update launch with CUDA events */
 };
+
+/* Counters of the work a handle has enqueued since the last cup_reset_stats.
+ * Device times are filled only while CUP_OPT_PROFILE is on; they are CUDA
+ * event intervals recorded on the launch stream around each Schur-update
+ * kernel and read after the call that launched it synchronised. */
+typedef struct {
+    int64_t launches;          /* kernels launched by the library */
+    int64_t host_syncs;        /* stream synchronisations made by the host driver */
+    int64_t tc_launches;       /* tcgen05 Schur-update kernels */
+    double tc_ms;              /* their summed device time */
+    double tc_limb_flops;      /* 2 L^2 M N K over those launches (bf16 tensor-core work) */
+    double tc_field_flops;     /* 2 M N K over those launches (field multiply + add) */
+    int64_t cc_launches;       /* CUDA-core Schur-update kernels */
+    double cc_ms;
+    double cc_field_flops;
+} cup_stats;
 
 /* Create a handle bound to CUDA device `device` (the device is made current
  * for the duration of each call). */
@@ -146,6 +163,12 @@ cup_status cup_rref(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64
 cup_status cup_solve(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda,
                      uint32_t *B, int64_t k, int64_t ldb, uint32_t *X, int64_t ldx, uint32_t p,
                      int64_t *rank, void *stream);
+
+/* Read (and keep) the counters of a handle. */
+cup_status cup_get_stats(cup_handle *handle, cup_stats *out);
+
+/* Zero the counters of a handle. */
+cup_status cup_reset_stats(cup_handle *handle);
 
 /* ---- Building blocks of the hot path (exposed for testing and reuse) ---- */
 

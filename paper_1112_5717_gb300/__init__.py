@@ -21,7 +21,19 @@ LIB_PATH = os.path.join(_HERE, "libcup_gb300.so")
 
 ENGINE_PLAIN = 0
 ENGINE_TENSOR = 1
-OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE = 0, 1, 2, 3, 4
+OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE, OPT_PROFILE = 0, 1, 2, 3, 4, 5
+
+
+class Stats(ctypes.Structure):
+    """Mirror of cup_stats (include/cup_gb300.h)."""
+    _fields_ = [("launches", ctypes.c_int64), ("host_syncs", ctypes.c_int64),
+                ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
+                ("tc_limb_flops", ctypes.c_double), ("tc_field_flops", ctypes.c_double),
+                ("cc_launches", ctypes.c_int64), ("cc_ms", ctypes.c_double),
+                ("cc_field_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 STATUS = {0: "CUP_OK", 1: "CUP_SINGULAR", 2: "CUP_INCONSISTENT", -1: "CUP_ERR_ARG",
           -2: "CUP_ERR_PRIME", -3: "CUP_ERR_VALUE", -4: "CUP_ERR_CUDA", -5: "CUP_ERR_TIMEOUT",
@@ -39,6 +51,8 @@ SIGNATURES = {
     "cup_destroy": (_INT, [_P]),
     "cup_set_option": (_INT, [_P, _INT, _I64]),
     "cup_last_cuda_error": (ctypes.c_char_p, [_P]),
+    "cup_get_stats": (_INT, [_P, _P]),
+    "cup_reset_stats": (_INT, [_P]),
     "cup_factor": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_rank_profile": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P]),
     "cup_det": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
@@ -114,7 +128,7 @@ class Handle:
         if engine is not None:
             self.set_option(OPT_ENGINE, engine)
         names = {"leaf_rows": OPT_LEAF_ROWS, "window": OPT_WINDOW, "tc_min_k": OPT_TC_MIN_K,
-                 "validate": OPT_VALIDATE}
+                 "validate": OPT_VALIDATE, "profile": OPT_PROFILE}
         for k, v in opts.items():
             self.set_option(names[k], int(v))
 
@@ -127,6 +141,14 @@ class Handle:
 
     def set_option(self, opt: int, value: int):
         self._check(self.lib.cup_set_option(self.h, opt, int(value)), "cup_set_option", self.h)
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self.lib.cup_get_stats(self.h, ctypes.byref(st)), "cup_get_stats", self.h)
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(self.lib.cup_reset_stats(self.h), "cup_reset_stats", self.h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -19,15 +19,16 @@
 #include <cstring>
 #include <cstdlib>
 #include <new>
+#include <vector>
 #include "cup_internal.cuh"
 #include "../../include/cup_gb300.h"
 
 struct cup_handle {
     int device = 0;
     int engine = CUP_ENGINE_TENSOR;
-    int leaf_rows = 32;
+    int leaf_rows = 64;
     int window = 64;
-    int64_t tc_min_k = 256;
+    int64_t tc_min_k = 64;
     int validate = 0;
     SlabScratch *d_slab = nullptr;
     int2 *d_pairs = nullptr;
@@ -37,6 +38,11 @@ struct cup_handle {
     int *d_err = nullptr;          // device-side error word of the tensor-core kernels
     void *d_ws = nullptr;          // limb planes of the tensor-core Schur update
     size_t ws_bytes = 0;
+    int profile = 0;
+    cup_stats stats = {};
+    struct Timed { cudaEvent_t e0, e1; double limb_flops, field_flops; bool tc; };
+    std::vector<Timed> pending;    // recorded intervals not yet read
+    std::vector<cudaEvent_t> evpool;
     char err[256] = {0};
 };
 
@@ -106,6 +112,42 @@ struct Ctx {
     cudaStream_t st;
 };
 
+cudaEvent_t take_event(cup_handle *h)
+{
+    if (!h->evpool.empty()) {
+        cudaEvent_t e = h->evpool.back();
+        h->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Fold recorded intervals into the counters; the stream they were recorded on
+// must have drained.
+void flush_timings(cup_handle *h)
+{
+    for (auto &t : h->pending) {
+        float ms = 0.f;
+        if (t.e0 && t.e1 && cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+            if (t.tc) h->stats.tc_ms += ms;
+            else h->stats.cc_ms += ms;
+        }
+        if (t.e0) h->evpool.push_back(t.e0);
+        if (t.e1) h->evpool.push_back(t.e1);
+    }
+    h->pending.clear();
+}
+
+cup_status sync_stream(cup_handle *h, cudaStream_t st)
+{
+    CU(cudaStreamSynchronize(st));
+    ++h->stats.host_syncs;
+    flush_timings(h);
+    return CUP_OK;
+}
+
 cup_status ensure_pairs(cup_handle *h, int64_t need)
 {
     if (need <= h->pairs_cap) return CUP_OK;
@@ -145,7 +187,7 @@ cup_status ensure_ws(cup_handle *h, size_t bytes)
 cup_status check_device_error(cup_handle *h, cudaStream_t st)
 {
     CU(cudaMemcpyAsync(h->h_pinned + 8, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
+    CK(sync_stream(h, st));
     if (h->h_pinned[8] != 0) {
         snprintf(h->err, sizeof(h->err), "device wait expired (site %d)", h->h_pinned[8]);
         cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
@@ -161,6 +203,7 @@ cup_status laswp(Ctx &c, int64_t row0, int64_t nrows, int64_t k0, int64_t k1)
     CK(ensure_pairs(h, k1 - k0));
     CU(launch_swaplist(c.ipiv, k0, k1, h->d_pairs, h->d_count, c.st));
     CU(launch_laswp(c.A, c.lda, row0, nrows, h->d_pairs, h->d_count, c.st));
+    h->stats.launches += 2;
     return CUP_OK;
 }
 
@@ -172,10 +215,26 @@ cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, in
     if (engine == CUP_ENGINE_TENSOR && K >= h->tc_min_k) {
         CK(ensure_base(h));
         CK(ensure_ws(h, tc_workspace_bytes(Mp.p, M, N, K)));
-        CU(launch_gemm_sub_tc(A, lda, B, ldb, C, ldc, M, N, K, Mp, h->d_ws, h->d_err, st));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->profile) { e0 = take_event(h); e1 = take_event(h); }
+        CU(launch_gemm_sub_tc(A, lda, B, ldb, C, ldc, M, N, K, Mp, h->d_ws, h->d_err, st, e0, e1));
+        const int L = tc_limbs(Mp.p);
+        const double f = 2.0 * (double)M * (double)N * (double)K;
+        h->stats.launches += 3;
+        h->stats.tc_launches += 1;
+        h->stats.tc_field_flops += f;
+        h->stats.tc_limb_flops += f * L * L;
+        if (h->profile) h->pending.push_back({e0, e1, f * L * L, f, true});
         return CUP_OK;
     }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profile) { e0 = take_event(h); e1 = take_event(h); if (e0) cudaEventRecord(e0, st); }
     CU(launch_gemm_sub_cc(A, lda, B, ldb, C, ldc, M, N, K, Mp, st));
+    if (e1) cudaEventRecord(e1, st);
+    h->stats.launches += 1;
+    h->stats.cc_launches += 1;
+    h->stats.cc_field_flops += 2.0 * (double)M * (double)N * (double)K;
+    if (h->profile) h->pending.push_back({e0, e1, 0.0, 2.0 * (double)M * (double)N * (double)K, false});
     return CUP_OK;
 }
 
@@ -183,12 +242,13 @@ cup_status trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t *B, 
                     int64_t m, int64_t n, const ModP &M, int engine, cudaStream_t st)
 {
     if (m <= 0 || n <= 0) return CUP_OK;
-    if (n <= 32) {
+    if (n <= 64) {
         CU(launch_trsm_ruu_leaf(U, ldu, B, ldb, m, (int)n, M, st));
+        h->stats.launches += 1;
         return CUP_OK;
     }
     // Algorithm 2: B1 <- B1 U1^{-1}; B2 <- B2 - B1 V; B2 <- B2 U2^{-1}
-    int64_t k = ((n / 2) + 31) / 32 * 32;
+    int64_t k = ((n / 2) + 63) / 64 * 64;
     CK(trsm_ruu(h, U, ldu, B, ldb, m, k, M, engine, st));
     CK(mm_sub(h, B + k, ldb, B, ldb, U + k, ldu, m, n - k, k, M, engine, st));
     CK(trsm_ruu(h, U + k * ldu + k, ldu, B + k, ldb, m, n - k, M, engine, st));
@@ -207,7 +267,8 @@ cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_ou
                               c.ipiv, c.prof, c.st));
         CU(cudaMemcpyAsync(h->h_pinned, h->d_slab, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
         CU(launch_slab_finish(c.A, c.lda, a, col0, w, c.M, h->d_slab, c.st));
-        CU(cudaStreamSynchronize(c.st));
+        h->stats.launches += 2;
+        CK(sync_stream(h, c.st));
         r1 = h->h_pinned[0];
         k = h->h_pinned[1];
         if (k == mrows) { *r_out = r1; return CUP_OK; }
@@ -278,6 +339,8 @@ cup_status cup_destroy(cup_handle *h)
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
         if (h->d_err) cudaFree(h->d_err);
         if (h->d_ws) cudaFree(h->d_ws);
+        flush_timings(h);
+        for (auto e : h->evpool) cudaEventDestroy(e);
     }
     delete h;
     return CUP_OK;
@@ -306,9 +369,27 @@ cup_status cup_set_option(cup_handle *h, int option, int64_t value)
     case CUP_OPT_VALIDATE:
         h->validate = value != 0;
         return CUP_OK;
+    case CUP_OPT_PROFILE:
+        h->profile = value != 0;
+        return CUP_OK;
     default:
         return CUP_ERR_ARG;
     }
+}
+
+cup_status cup_get_stats(cup_handle *h, cup_stats *out)
+{
+    if (!h || !out) return CUP_ERR_ARG;
+    *out = h->stats;
+    return CUP_OK;
+}
+
+cup_status cup_reset_stats(cup_handle *h)
+{
+    if (!h) return CUP_ERR_ARG;
+    flush_timings(h);
+    h->stats = cup_stats{};
+    return CUP_OK;
 }
 
 const char *cup_last_cuda_error(cup_handle *h)
@@ -422,7 +503,8 @@ cup_status cup_det(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t 
             if (s == CUP_OK)
                 s = cuda_ok(h, cudaMemcpyAsync(h->h_pinned, d_out, sizeof(uint32_t),
                                                cudaMemcpyDeviceToHost, (cudaStream_t)stream));
-            if (s == CUP_OK) s = cuda_ok(h, cudaStreamSynchronize((cudaStream_t)stream));
+            if (s == CUP_OK) s = sync_stream(h, (cudaStream_t)stream);
+            h->stats.launches += 1;
             if (s == CUP_OK) *det = (uint32_t)h->h_pinned[0];
         }
     }

@@ -49,4 +49,4 @@ int tc_limbs(uint32_t p);
 size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K);
 cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
-                               cudaStream_t st);
+                               cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);

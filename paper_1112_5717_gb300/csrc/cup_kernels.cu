@@ -32,7 +32,7 @@
 // to the remaining rows (TRSM + MM, as at an internal node of Algorithm 6) and
 // calls the kernel again on them.
 // ---------------------------------------------------------------------------
-#define PIV_THREADS 256
+#define PIV_THREADS 512
 #define PIV_LDW (CUP_WNMAX + CUP_BMAX + 1)
 
 __global__ void __launch_bounds__(PIV_THREADS)
@@ -108,21 +108,25 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         }
         const uint32_t f = W[i * PIV_LDW + r];
         if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
-        // rows below: window positions (r, wne) and T columns [0, i]
+        // rows below: window positions (r, wne) and T columns [0, i]; 64 column
+        // slots x (nt / 64) row groups, no index division
         const int nwin = wne - r - 1;
         const int ncols = nwin + i + 1;
-        const int nrows = brows - i - 1;
-        for (int idx = tid; idx < nrows * ncols; idx += nt) {
-            int di = idx / ncols, j = idx - di * ncols;
-            int ii = i + 1 + di;
-            uint32_t m = W[ii * PIV_LDW + r];
-            if (j < nwin) {
-                int q = r + 1 + j;
-                W[ii * PIV_LDW + q] = ffupd(f, W[ii * PIV_LDW + q], m, W[i * PIV_LDW + q], M);
-            } else {
-                int jj = j - nwin;             // T column jj <= i; T[i][i] is the product Sprod
-                uint32_t y = (jj == i) ? Sprod : W[i * PIV_LDW + TC + jj];
-                W[ii * PIV_LDW + TC + jj] = ffupd(f, W[ii * PIV_LDW + TC + jj], m, y, M);
+        {
+            const int cx = tid & 63, ry = tid >> 6, nry = nt >> 6;
+            for (int ii = i + 1 + ry; ii < brows; ii += nry) {
+                uint32_t *wr = W + ii * PIV_LDW;
+                const uint32_t m = wr[r];
+                for (int j = cx; j < ncols; j += 64) {
+                    if (j < nwin) {
+                        const int q = r + 1 + j;
+                        wr[q] = ffupd(f, wr[q], m, W[i * PIV_LDW + q], M);
+                    } else {
+                        const int jj = j - nwin;   // T column jj <= i; T[i][i] is the product Sprod
+                        const uint32_t y = (jj == i) ? Sprod : W[i * PIV_LDW + TC + jj];
+                        wr[TC + jj] = ffupd(f, wr[TC + jj], m, y, M);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -133,9 +137,21 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 
     for (int t = tid; t < rs; t += nt) s_finv[t] = invm(s_f[t], M);
     __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = 1u % M.p;
-        for (int t = 0; t < rs; ++t) { s_Sinv[t] = acc; acc = mulm(acc, s_finv[t], M); }
+    if (warp == 0) {
+        // exclusive prefix products Sinv[t] = prod_{t' < t} finv[t'] (two 32-element scans)
+        uint32_t carry = 1u % M.p;
+        for (int base = 0; base < rs; base += 32) {
+            const int t = base + lane;
+            uint32_t v = (t < rs) ? s_finv[t] : 1u % M.p;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = mulm(v, u, M);
+            }
+            uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+            if (lane == 0) ex = 1u % M.p;
+            if (t < rs) s_Sinv[t] = mulm(carry, ex, M);
+            carry = mulm(carry, __shfl_sync(0xffffffffu, v, 31), M);
+        }
     }
     __syncthreads();
 
@@ -153,23 +169,31 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         else if (u == t) v = mulm(s_Sfwd[t], s_finv[t], M);
         S->Minv[t][u] = v;
     }
-    __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 1];
-    if (tid == 0) {
+    __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
+    if (warp == 0) {
         int ns = 0;
-        for (int q = 0; q < wne; ++q) {
-            int sl = (s_wcol[q] != q) ? ns++ : -1;
-            S->win_col[q] = s_wcol[q];
-            S->win_slot[q] = sl;
-            if (sl >= 0) s_sorig[sl] = s_wcol[q];
+        for (int base = 0; base < wne; base += 32) {
+            const int q = base + lane;
+            const bool disp = (q < wne) && (s_wcol[q] != q);
+            const unsigned bal = __ballot_sync(0xffffffffu, disp);
+            const int sl = disp ? ns + __popc(bal & ((1u << lane) - 1u)) : -1;
+            if (q < wne) {
+                S->win_col[q] = s_wcol[q];
+                S->win_slot[q] = sl;
+                if (disp) s_sorig[sl] = s_wcol[q];
+            }
+            ns += __popc(bal);
         }
-        S->ext_pos = s_ext;
-        S->ext_slot = -1;
-        if (s_ext >= 0) { S->ext_slot = ns; s_sorig[ns] = 0; ++ns; }
-        s_slot[0] = ns;
-        S->n_slot = ns;
-        S->r_s = rs;
-        S->i_stop = stop;
-        S->wne = wne;
+        if (lane == 0) {
+            S->ext_pos = s_ext;
+            S->ext_slot = -1;
+            if (s_ext >= 0) { S->ext_slot = ns; s_sorig[ns] = 0; ++ns; }
+            s_slot[0] = ns;
+            S->n_slot = ns;
+            S->r_s = rs;
+            S->i_stop = stop;
+            S->wne = wne;
+        }
     }
     for (int t = tid; t < rs; t += nt) {
         S->prof[t] = s_prof[t];
@@ -329,36 +353,38 @@ k_laswp(uint32_t *__restrict__ A, int64_t lda, int64_t row0, int64_t nrows,
 
 // ---------------------------------------------------------------------------
 // TRSM(Right, Upper, Unit) leaf: B[:, 0:n) <- B[:, 0:n) U^{-1} for an n x n
-// (n <= 32) unit upper block U; one thread per row, forward substitution
-// x_j = b_j - sum_{k<j} x_k u_kj (Algorithm 2 at its base, unit diagonal).
+// (n <= 64) unit upper block U (Algorithm 2 at its base, unit diagonal).
+// One warp per row: lane j holds columns j and j + 32; at step k the final
+// x_k is broadcast and every later column subtracts x_k u_kj.
 // ---------------------------------------------------------------------------
-#define TRSM_LEAF 32
-__global__ void __launch_bounds__(128)
+#define TRSM_LEAF 64
+#define TRSM_WARPS 8
+__global__ void __launch_bounds__(32 * TRSM_WARPS)
 k_trsm_ruu_leaf(const uint32_t *__restrict__ U, int64_t ldu, uint32_t *__restrict__ B, int64_t ldb,
                 int64_t m, int n, ModP M)
 {
-    __shared__ uint32_t sU[TRSM_LEAF][TRSM_LEAF + 1];
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        int k = idx / n, j = idx - k * n;
-        sU[k][j] = (j > k) ? U[k * ldu + j] : 0u;
+    __shared__ uint32_t sU[TRSM_LEAF][TRSM_LEAF];
+    for (int idx = threadIdx.x; idx < TRSM_LEAF * TRSM_LEAF; idx += blockDim.x) {
+        int k = idx / TRSM_LEAF, j = idx - k * TRSM_LEAF;
+        sU[k][j] = (j > k && j < n && k < n) ? U[k * ldu + j] : 0u;
     }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    uint32_t *row = B + i * ldb;
-    uint32_t x[TRSM_LEAF];
-#pragma unroll
-    for (int j = 0; j < TRSM_LEAF; ++j) x[j] = (j < n) ? row[j] : 0u;
-#pragma unroll
-    for (int j = 1; j < TRSM_LEAF; ++j) {
-        Acc acc = {0ull, 0u};
-#pragma unroll
-        for (int k = 0; k < j; ++k) acc_add(acc, (uint64_t)x[k] * sU[k][j]);
-        x[j] = subm(x[j], acc_red(acc, M), M);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * TRSM_WARPS;
+    for (int64_t i = (int64_t)blockIdx.x * TRSM_WARPS + (threadIdx.x >> 5); i < m; i += nw) {
+        uint32_t *row = B + i * ldb;
+        uint32_t x0 = (lane < n) ? row[lane] : 0u;
+        uint32_t x1 = (lane + 32 < n) ? row[lane + 32] : 0u;
+        for (int k = 0; k < n; ++k) {
+            const uint32_t xk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
+            if (xk) {
+                x0 = subm(x0, mulm(xk, sU[k][lane], M), M);
+                x1 = subm(x1, mulm(xk, sU[k][lane + 32], M), M);
+            }
+        }
+        if (lane < n) row[lane] = x0;
+        if (lane + 32 < n) row[lane + 32] = x1;
     }
-#pragma unroll
-    for (int j = 0; j < TRSM_LEAF; ++j)
-        if (j < n) row[j] = x[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -483,8 +509,10 @@ cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, in
                                  int64_t m, int n, ModP M, cudaStream_t st)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    int64_t nb = (m + 127) / 128;
-    k_trsm_ruu_leaf<<<(unsigned)nb, 128, 0, st>>>(U, ldu, B, ldb, m, n, M);
+    if (n > TRSM_LEAF) return cudaErrorInvalidValue;
+    int64_t nb = (m + TRSM_WARPS - 1) / TRSM_WARPS;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_trsm_ruu_leaf<<<(unsigned)nb, 32 * TRSM_WARPS, 0, st>>>(U, ldu, B, ldb, m, n, M);
     return cudaGetLastError();
 }
 

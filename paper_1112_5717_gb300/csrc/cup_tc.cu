@@ -430,7 +430,8 @@ bool make_map(CUtensorMap *map, void *base, int kp, int rows, int L, int box_row
 
 template <int L>
 cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C, int64_t ldc,
-                int M, int N, int K, ModP Mp, void *ws, int *err, cudaStream_t st)
+                int M, int N, int K, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0,
+                cudaEvent_t ev1)
 {
     using CF = Cfg<L>;
     const int Kp = (K + BK - 1) / BK * BK;
@@ -456,8 +457,11 @@ cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, 
     const uint64_t off = ((1ull << bound_bits) / Mp.p + 1) * Mp.p;
     const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
     dim3 grid((N + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
+    if (ev0) cudaEventRecord(ev0, st);
     k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, C, ldc, M, N, Kp, Mp, off, sh32, err);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (ev1) cudaEventRecord(ev1, st);
+    return e;
 }
 
 }  // namespace tc
@@ -479,14 +483,14 @@ size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K)
 
 cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
-                               cudaStream_t st)
+                               cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2) return cudaErrorInvalidValue;
     switch (tc_limbs(Mp.p)) {
-    case 1: return tc::run<1>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
-    case 2: return tc::run<2>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
-    case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
-    default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st);
+    case 1: return tc::run<1>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
+    case 2: return tc::run<2>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
+    case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
+    default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
     }
 }
