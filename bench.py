@@ -54,6 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--leaf-rows", type=int, default=None)
     ap.add_argument("--window", type=int, default=None)
     ap.add_argument("--tc-min-k", type=int, default=None)
+    ap.add_argument("--profile", type=int, default=1, help="library timing level (2: every kernel class)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only warm-up and timed factorisations (for profiler launch lists)")
     return ap.parse_args(argv)
@@ -222,7 +223,7 @@ def run_ours(args):
     A = torch.empty_like(A0)
     opts = {k: v for k, v in (("leaf_rows", args.leaf_rows), ("window", args.window),
                               ("tc_min_k", args.tc_min_k)) if v is not None}
-    h = cup.Handle(dev, engine=engine, profile=1, **opts)
+    h = cup.Handle(dev, engine=engine, profile=args.profile, **opts)
     stream = torch.cuda.current_stream()
 
     def one_step():
@@ -293,6 +294,8 @@ def run_ours(args):
                               "achieved": st["cc_field_flops"] / (st["cc_ms"] * 1e-3) / 1e12,
                               "peak": None, "unit": "Tfield-op/s", "frac": None, "traffic": None}
     result["stats"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
+    if args.profile >= 2:
+        result["class_ms_per_step"] = {k: round(v / args.steps, 3) for k, v in h.class_ms().items() if v}
 
     if args.kernel_only:
         if rank == 0:

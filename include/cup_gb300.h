@@ -60,10 +60,10 @@ enum {
 enum {
     CUP_OPT_ENGINE = 0,        /* CUP_ENGINE_PLAIN or CUP_ENGINE_TENSOR (default TENSOR) */
     CUP_OPT_LEAF_ROWS = 1,     /* rows of a base-case slab, 1..64 (default 64) */
-    CUP_OPT_WINDOW = 2,        /* pivot-search window of the base case, 1..128 (default 64) */
+    CUP_OPT_WINDOW = 2,        /* pivot-search window of the base case, 1..128 (default 96) */
     CUP_OPT_TC_MIN_K = 3,      /* smallest inner dimension sent to the tensor engine (default 64) */
     CUP_OPT_VALIDATE = 4,      /* nonzero: check inputs are canonical residues (slow) */
-    CUP_OPT_PROFILE = 5        /* nonzero: time every Schur-update launch with CUDA events */
+    CUP_OPT_PROFILE = 5        /* 1: time every Schur-update launch with CUDA events; 2: every launch */
 };
 
 /* Counters of the work a handle has enqueued since the last cup_reset_stats.
@@ -167,6 +167,12 @@ cup_status cup_solve(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int6
 /* Read (and keep) the counters of a handle. */
 cup_status cup_get_stats(cup_handle *handle, cup_stats *out);
 
+/* Device time per kernel class, filled while CUP_OPT_PROFILE >= 2 (every
+ * launch bracketed by events): out8[0] tensor-core Schur update, [1]
+ * CUDA-core Schur update, [2] base-case pivot kernel, [3] base-case finish
+ * kernel, [4] TRSM leaf, [5] column transpositions, [6..7] unused. */
+cup_status cup_class_ms(cup_handle *handle, double *out8);
+
 /* Zero the counters of a handle. */
 cup_status cup_reset_stats(cup_handle *handle);
 
@@ -184,6 +190,36 @@ cup_status cup_mm_sub(cup_handle *handle, uint32_t *C, int64_t ldc, const uint32
  * upper triangle is read. B is m x n (ldb). */
 cup_status cup_trsm_ruu(cup_handle *handle, const uint32_t *U, int64_t ldu, uint32_t *B,
                         int64_t ldb, int64_t m, int64_t n, uint32_t p, void *stream);
+
+/* Triangle selection for cup_trsm / cup_trmm / cup_trtri (bit flags). */
+enum {
+    CUP_LEFT = 1,              /* set: B <- op(T) B; clear: B <- B op(T) */
+    CUP_UPPER = 2,             /* set: T upper triangular; clear: lower */
+    CUP_UNIT = 4               /* set: unit diagonal (the stored diagonal is not read) */
+};
+
+/* TRSM in any of its eight variants (Sec. 3.2; Algorithm 2 is Right, Upper,
+ * NonUnit): B <- T^{-1} B (CUP_LEFT) or B <- B T^{-1}. T is n x n (ldt), only
+ * its selected triangle (and diagonal unless CUP_UNIT) is read; n = rows of B
+ * for CUP_LEFT, columns of B otherwise. B is rows x cols (ldb), overwritten. */
+cup_status cup_trsm(cup_handle *handle, int flags, const uint32_t *T, int64_t ldt, uint32_t *B,
+                    int64_t ldb, int64_t rows, int64_t cols, uint32_t p, void *stream);
+
+/* TRMM (Sec. 3.2, same eight variants): B <- T B (CUP_LEFT) or B <- B T. */
+cup_status cup_trmm(cup_handle *handle, int flags, const uint32_t *T, int64_t ldt, uint32_t *B,
+                    int64_t ldb, int64_t rows, int64_t cols, uint32_t p, void *stream);
+
+/* TRTRI (Algorithm 3 and its variants): T <- T^{-1} in place for an n x n
+ * triangle selected by CUP_UPPER / CUP_UNIT (CUP_LEFT ignored); entries outside
+ * the triangle (and the diagonal when CUP_UNIT) are not touched. The diagonal
+ * of a non-unit triangle must be nonzero. */
+cup_status cup_trtri(cup_handle *handle, int flags, uint32_t *T, int64_t ldt, int64_t n, uint32_t p,
+                     void *stream);
+
+/* TRULM (Algorithm 4): A = [L\U] n x n with U unit upper triangular stored
+ * strictly above the diagonal and L lower triangular stored on and below it;
+ * A <- U L in place. */
+cup_status cup_trulm(cup_handle *handle, uint32_t *A, int64_t lda, int64_t n, uint32_t p, void *stream);
 
 /* Column transpositions (Sec. 1.1): for t = k0..k1-1 in order, swap columns t
  * and d_ipiv[t] of rows row0..row0+nrows-1 of A (A <- A P^T restricted to

@@ -53,6 +53,7 @@ SIGNATURES = {
     "cup_last_cuda_error": (ctypes.c_char_p, [_P]),
     "cup_get_stats": (_INT, [_P, _P]),
     "cup_reset_stats": (_INT, [_P]),
+    "cup_class_ms": (_INT, [_P, _P]),
     "cup_factor": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_rank_profile": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P]),
     "cup_det": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
@@ -62,7 +63,13 @@ SIGNATURES = {
     "cup_mm_sub": (_INT, [_P, _P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _INT, _P]),
     "cup_trsm_ruu": (_INT, [_P, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
     "cup_laswp_cols": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P]),
+    "cup_trsm": (_INT, [_P, _INT, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
+    "cup_trmm": (_INT, [_P, _INT, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
+    "cup_trtri": (_INT, [_P, _INT, _P, _I64, _I64, _U32, _P]),
+    "cup_trulm": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
 }
+
+LEFT, UPPER, UNIT = 1, 2, 4
 
 _lib = None
 
@@ -146,6 +153,12 @@ class Handle:
         st = Stats()
         self._check(self.lib.cup_get_stats(self.h, ctypes.byref(st)), "cup_get_stats", self.h)
         return st.as_dict()
+
+    def class_ms(self) -> dict:
+        arr = (ctypes.c_double * 8)()
+        self._check(self.lib.cup_class_ms(self.h, arr), "cup_class_ms", self.h)
+        names = ["tc_gemm", "cc_gemm", "slab_pivots", "slab_finish", "trsm_leaf", "laswp", "r6", "r7"]
+        return {k: arr[i] for i, k in enumerate(names)}
 
     def reset_stats(self):
         self._check(self.lib.cup_reset_stats(self.h), "cup_reset_stats", self.h)
@@ -255,6 +268,40 @@ class Handle:
         st = self.lib.cup_trsm_ruu(self.h, U.data_ptr(), ldu, B.data_ptr(), ldb, m, n, p,
                                    _stream_ptr(stream))
         self._check(st, "cup_trsm_ruu", self.h)
+
+    def trsm(self, flags: int, T, B, p: int, stream=None):
+        """B <- T^{-1} B (LEFT) or B T^{-1}; flags from LEFT | UPPER | UNIT."""
+        n, n2, ldt = _mat(T, "T")
+        rows, cols, ldb = _mat(B, "B")
+        if n != n2 or n != (rows if flags & LEFT else cols):
+            raise ValueError("shape mismatch")
+        st = self.lib.cup_trsm(self.h, flags, T.data_ptr(), ldt, B.data_ptr(), ldb, rows, cols, p,
+                               _stream_ptr(stream))
+        self._check(st, "cup_trsm", self.h)
+
+    def trmm(self, flags: int, T, B, p: int, stream=None):
+        """B <- T B (LEFT) or B T; flags from LEFT | UPPER | UNIT."""
+        n, n2, ldt = _mat(T, "T")
+        rows, cols, ldb = _mat(B, "B")
+        if n != n2 or n != (rows if flags & LEFT else cols):
+            raise ValueError("shape mismatch")
+        st = self.lib.cup_trmm(self.h, flags, T.data_ptr(), ldt, B.data_ptr(), ldb, rows, cols, p,
+                               _stream_ptr(stream))
+        self._check(st, "cup_trmm", self.h)
+
+    def trtri(self, flags: int, T, p: int, stream=None):
+        n, n2, ldt = _mat(T, "T")
+        if n != n2:
+            raise ValueError("square triangle needed")
+        st = self.lib.cup_trtri(self.h, flags, T.data_ptr(), ldt, n, p, _stream_ptr(stream))
+        self._check(st, "cup_trtri", self.h)
+
+    def trulm(self, A, p: int, stream=None):
+        n, n2, lda = _mat(A, "A")
+        if n != n2:
+            raise ValueError("square matrix needed")
+        st = self.lib.cup_trulm(self.h, A.data_ptr(), lda, n, p, _stream_ptr(stream))
+        self._check(st, "cup_trulm", self.h)
 
     def laswp_cols(self, A, ipiv, k0: int, k1: int, row0: int = 0, nrows: int | None = None,
                    stream=None):

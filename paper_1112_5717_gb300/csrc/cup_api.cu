@@ -27,7 +27,7 @@ struct cup_handle {
     int device = 0;
     int engine = CUP_ENGINE_TENSOR;
     int leaf_rows = 64;
-    int window = 64;
+    int window = 96;
     int64_t tc_min_k = 64;
     int validate = 0;
     SlabScratch *d_slab = nullptr;
@@ -40,7 +40,8 @@ struct cup_handle {
     size_t ws_bytes = 0;
     int profile = 0;
     cup_stats stats = {};
-    struct Timed { cudaEvent_t e0, e1; double limb_flops, field_flops; bool tc; };
+    struct Timed { cudaEvent_t e0, e1; double limb_flops, field_flops; int cls; };
+    double cls_ms[8] = {0};        // per kernel class, profile level >= 2
     std::vector<Timed> pending;    // recorded intervals not yet read
     std::vector<cudaEvent_t> evpool;
     char err[256] = {0};
@@ -131,8 +132,9 @@ void flush_timings(cup_handle *h)
     for (auto &t : h->pending) {
         float ms = 0.f;
         if (t.e0 && t.e1 && cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
-            if (t.tc) h->stats.tc_ms += ms;
-            else h->stats.cc_ms += ms;
+            if (t.cls == 0) h->stats.tc_ms += ms;
+            else if (t.cls == 1) h->stats.cc_ms += ms;
+            h->cls_ms[t.cls] += ms;
         }
         if (t.e0) h->evpool.push_back(t.e0);
         if (t.e1) h->evpool.push_back(t.e1);
@@ -147,6 +149,26 @@ cup_status sync_stream(cup_handle *h, cudaStream_t st)
     flush_timings(h);
     return CUP_OK;
 }
+
+// Interval of one kernel class (profile level >= 2): classes 2 = base-case
+// pivots, 3 = base-case finish, 4 = TRSM leaf, 5 = transpositions, 6 = limb split.
+struct ClassTimer {
+    cup_handle *h;
+    cudaStream_t st;
+    int cls;
+    cudaEvent_t e0 = nullptr;
+    ClassTimer(cup_handle *h_, cudaStream_t st_, int cls_) : h(h_), st(st_), cls(cls_)
+    {
+        if (h->profile >= 2 && (e0 = take_event(h))) cudaEventRecord(e0, st);
+    }
+    ~ClassTimer()
+    {
+        if (!e0) return;
+        cudaEvent_t e1 = take_event(h);
+        if (e1) cudaEventRecord(e1, st);
+        h->pending.push_back({e0, e1, 0.0, 0.0, cls});
+    }
+};
 
 cup_status ensure_pairs(cup_handle *h, int64_t need)
 {
@@ -201,6 +223,7 @@ cup_status laswp(Ctx &c, int64_t row0, int64_t nrows, int64_t k0, int64_t k1)
     cup_handle *h = c.h;
     if (nrows <= 0 || k1 <= k0) return CUP_OK;
     CK(ensure_pairs(h, k1 - k0));
+    ClassTimer tm(h, c.st, 5);
     CU(launch_swaplist(c.ipiv, k0, k1, h->d_pairs, h->d_count, c.st));
     CU(launch_laswp(c.A, c.lda, row0, nrows, h->d_pairs, h->d_count, c.st));
     h->stats.launches += 2;
@@ -209,7 +232,7 @@ cup_status laswp(Ctx &c, int64_t row0, int64_t nrows, int64_t k0, int64_t k1)
 
 cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
                   const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K, const ModP &Mp,
-                  int engine, cudaStream_t st)
+                  int engine, cudaStream_t st, int add = 0)
 {
     if (M <= 0 || N <= 0 || K <= 0) return CUP_OK;
     if (engine == CUP_ENGINE_TENSOR && K >= h->tc_min_k) {
@@ -217,24 +240,24 @@ cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, in
         CK(ensure_ws(h, tc_workspace_bytes(Mp.p, M, N, K)));
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->profile) { e0 = take_event(h); e1 = take_event(h); }
-        CU(launch_gemm_sub_tc(A, lda, B, ldb, C, ldc, M, N, K, Mp, h->d_ws, h->d_err, st, e0, e1));
+        CU(launch_gemm_sub_tc(A, lda, B, ldb, C, ldc, M, N, K, Mp, h->d_ws, h->d_err, st, e0, e1, add));
         const int L = tc_limbs(Mp.p);
         const double f = 2.0 * (double)M * (double)N * (double)K;
         h->stats.launches += 3;
         h->stats.tc_launches += 1;
         h->stats.tc_field_flops += f;
         h->stats.tc_limb_flops += f * L * L;
-        if (h->profile) h->pending.push_back({e0, e1, f * L * L, f, true});
+        if (h->profile) h->pending.push_back({e0, e1, f * L * L, f, 0});
         return CUP_OK;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profile) { e0 = take_event(h); e1 = take_event(h); if (e0) cudaEventRecord(e0, st); }
-    CU(launch_gemm_sub_cc(A, lda, B, ldb, C, ldc, M, N, K, Mp, st));
+    CU(launch_gemm_sub_cc(A, lda, B, ldb, C, ldc, M, N, K, Mp, st, add));
     if (e1) cudaEventRecord(e1, st);
     h->stats.launches += 1;
     h->stats.cc_launches += 1;
     h->stats.cc_field_flops += 2.0 * (double)M * (double)N * (double)K;
-    if (h->profile) h->pending.push_back({e0, e1, 0.0, 2.0 * (double)M * (double)N * (double)K, false});
+    if (h->profile) h->pending.push_back({e0, e1, 0.0, 2.0 * (double)M * (double)N * (double)K, 1});
     return CUP_OK;
 }
 
@@ -243,6 +266,7 @@ cup_status trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t *B, 
 {
     if (m <= 0 || n <= 0) return CUP_OK;
     if (n <= 64) {
+        ClassTimer tm(h, st, 4);
         CU(launch_trsm_ruu_leaf(U, ldu, B, ldb, m, (int)n, M, st));
         h->stats.launches += 1;
         return CUP_OK;
@@ -255,6 +279,145 @@ cup_status trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t *B, 
     return CUP_OK;
 }
 
+// Triangular solve or multiply with an n x n triangle T (Sec. 3.2): right side
+// B (rows x n) <- B T^{-1} or B T; left side B (n x cols) <- T^{-1} B or T B.
+// Halves the triangle (Algorithm 2 and its mirror images; TRMM in the same
+// way) and sends the off-diagonal products to the Schur-update engine.
+cup_status tri_op(cup_handle *h, int flags, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
+                  int64_t rows, int64_t cols, const ModP &M, int engine, cudaStream_t st)
+{
+    const bool left = flags & TRI_LEFT, upper = flags & TRI_UPPER, solve = flags & TRI_SOLVE;
+    const int64_t n = left ? rows : cols;
+    if (rows <= 0 || cols <= 0) return CUP_OK;
+    if (n <= 64) {
+        ClassTimer tm(h, st, 4);
+        CU(launch_tri_leaf(flags, T, ldt, B, ldb, rows, cols, M, st));
+        h->stats.launches += 1;
+        return CUP_OK;
+    }
+    const int64_t k = ((n / 2) + 63) / 64 * 64;
+    const uint32_t *T11 = T, *T12 = T + k, *T21 = T + k * ldt, *T22 = T + k * ldt + k;
+    if (!left) {
+        uint32_t *B1 = B, *B2 = B + k;
+        const int64_t m = rows, n2 = n - k;
+        if (solve && upper) {
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, m, k, M, engine, st));
+            CK(mm_sub(h, B2, ldb, B1, ldb, T12, ldt, m, n2, k, M, engine, st, 0));
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, m, n2, M, engine, st));
+        } else if (solve) {
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, m, n2, M, engine, st));
+            CK(mm_sub(h, B1, ldb, B2, ldb, T21, ldt, m, k, n2, M, engine, st, 0));
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, m, k, M, engine, st));
+        } else if (upper) {
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, m, n2, M, engine, st));
+            CK(mm_sub(h, B2, ldb, B1, ldb, T12, ldt, m, n2, k, M, engine, st, 1));
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, m, k, M, engine, st));
+        } else {
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, m, k, M, engine, st));
+            CK(mm_sub(h, B1, ldb, B2, ldb, T21, ldt, m, k, n2, M, engine, st, 1));
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, m, n2, M, engine, st));
+        }
+    } else {
+        uint32_t *B1 = B, *B2 = B + k * ldb;
+        const int64_t c = cols, n2 = n - k;
+        if (solve && upper) {
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, n2, c, M, engine, st));
+            CK(mm_sub(h, B1, ldb, T12, ldt, B2, ldb, k, c, n2, M, engine, st, 0));
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, k, c, M, engine, st));
+        } else if (solve) {
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, k, c, M, engine, st));
+            CK(mm_sub(h, B2, ldb, T21, ldt, B1, ldb, n2, c, k, M, engine, st, 0));
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, n2, c, M, engine, st));
+        } else if (upper) {
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, k, c, M, engine, st));
+            CK(mm_sub(h, B1, ldb, T12, ldt, B2, ldb, k, c, n2, M, engine, st, 1));
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, n2, c, M, engine, st));
+        } else {
+            CK(tri_op(h, flags, T22, ldt, B2, ldb, n2, c, M, engine, st));
+            CK(mm_sub(h, B2, ldb, T21, ldt, B1, ldb, n2, c, k, M, engine, st, 1));
+            CK(tri_op(h, flags, T11, ldt, B1, ldb, k, c, M, engine, st));
+        }
+    }
+    return CUP_OK;
+}
+
+// TRTRI (Algorithm 3 and its lower-triangular mirror): T <- T^{-1} in place.
+// Upper: V <- V U2^{-1}, V <- U1^{-1} V, V <- -V, then recurse on U1, U2.
+// Lower: W <- L2^{-1} W, W <- W L1^{-1}, W <- -W, then recurse.
+cup_status trtri(cup_handle *h, bool upper, bool unit, uint32_t *T, int64_t ldt, int64_t n, const ModP &M,
+                 int engine, cudaStream_t st)
+{
+    if (n <= 0) return CUP_OK;
+    if (n <= 64) {
+        ClassTimer tm(h, st, 4);
+        CU(launch_trtri_leaf(upper, unit, T, ldt, (int)n, M, st));
+        h->stats.launches += 1;
+        return CUP_OK;
+    }
+    const int64_t k = ((n / 2) + 63) / 64 * 64, n2 = n - k;
+    uint32_t *T11 = T, *T12 = T + k, *T21 = T + k * ldt, *T22 = T + k * ldt + k;
+    const int base = (upper ? TRI_UPPER : 0) | (unit ? TRI_UNIT : 0) | TRI_SOLVE;
+    if (upper) {
+        CK(tri_op(h, base, T22, ldt, T12, ldt, k, n2, M, engine, st));
+        CK(tri_op(h, base | TRI_LEFT, T11, ldt, T12, ldt, k, n2, M, engine, st));
+        CU(launch_negate(T12, ldt, k, n2, M.p, st));
+    } else {
+        CK(tri_op(h, base | TRI_LEFT, T22, ldt, T21, ldt, n2, k, M, engine, st));
+        CK(tri_op(h, base, T11, ldt, T21, ldt, n2, k, M, engine, st));
+        CU(launch_negate(T21, ldt, n2, k, M.p, st));
+    }
+    h->stats.launches += 1;
+    CK(trtri(h, upper, unit, T11, ldt, k, M, engine, st));
+    CK(trtri(h, upper, unit, T22, ldt, n2, M, engine, st));
+    return CUP_OK;
+}
+
+// TRULM (Algorithm 4) for A = [L\U] with U unit upper (strictly above the
+// diagonal) and L non-unit lower (on and below it): A <- U L in place.
+cup_status trulm(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, const ModP &M, int engine, cudaStream_t st)
+{
+    if (n <= 0) return CUP_OK;
+    if (n <= 64) {
+        ClassTimer tm(h, st, 4);
+        CU(launch_trulm_leaf(A, lda, (int)n, M, st));
+        h->stats.launches += 1;
+        return CUP_OK;
+    }
+    const int64_t k = ((n / 2) + 63) / 64 * 64, n2 = n - k;
+    uint32_t *A11 = A, *A12 = A + k, *A21 = A + k * lda, *A22 = A + k * lda + k;
+    CK(trulm(h, A11, lda, k, M, engine, st));                                           // U1 L1
+    CK(mm_sub(h, A11, lda, A12, lda, A21, lda, k, k, n2, M, engine, st, 1));            // + U2 L2
+    CK(tri_op(h, 0, A22, lda, A12, lda, k, n2, M, engine, st));                         // U2 L3
+    CK(tri_op(h, TRI_LEFT | TRI_UPPER | TRI_UNIT, A22, lda, A21, lda, n2, k, M, engine, st));  // U3 L2
+    CK(trulm(h, A22, lda, n2, M, engine, st));                                          // U3 L3
+    return CUP_OK;
+}
+
+// Algorithms 7 and 8 on the [C\U] factors of rank r: leaves A as
+// [X1 X2; R2 0] with the rows of C reordered by the profile loop, i.e. the
+// reduced column echelon transform up to that row permutation.
+cup_status red_col_ech(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, int64_t r,
+                       const int64_t *d_prof, const ModP &M, int engine, cudaStream_t st)
+{
+    if (r <= 0) return CUP_OK;
+    // Algorithm 7: M <- U1^{-1} U2, N <- -M, U1 <- U1^{-1}
+    if (r < n) {
+        CK(tri_op(h, TRI_LEFT | TRI_UPPER | TRI_UNIT | TRI_SOLVE, A, lda, A + r, lda, r, n - r, M, engine, st));
+        CU(launch_negate(A + r, lda, r, n - r, M.p, st));
+        h->stats.launches += 1;
+    }
+    CK(trtri(h, true, true, A, lda, r, M, engine, st));
+    // Algorithm 8: bring the profile rows of C to the top (first j+1 entries of
+    // rows j and i_j exchanged, j increasing), R2 <- L2 L1^{-1}, L1 <- L1^{-1},
+    // X1 <- T1 L1^{-1}
+    CU(launch_row_swaps(A, lda, r, d_prof, r, 0, 0, 0, 1, st));
+    h->stats.launches += 1;
+    if (m > r) CK(tri_op(h, TRI_SOLVE, A, lda, A + r * lda, lda, m - r, r, M, engine, st));
+    CK(trtri(h, false, false, A, lda, r, M, engine, st));
+    CK(trulm(h, A, lda, r, M, engine, st));
+    return CUP_OK;
+}
+
 cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_out)
 {
     cup_handle *h = c.h;
@@ -263,10 +426,16 @@ cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_ou
     if (w <= 0 || mrows <= 0) return CUP_OK;
     int64_t k, r1;
     if (mrows <= h->leaf_rows) {
-        CU(launch_slab_pivots(c.A, c.lda, a, (int)mrows, col0, w, h->window, c.M, h->d_slab,
+        {
+        ClassTimer tm(h, c.st, 2);
+        CU(launch_slab_pivots(c.A, c.lda, a, (int)mrows, col0, w, h->window, 0, c.M, h->d_slab,
                               c.ipiv, c.prof, c.st));
+        }
         CU(cudaMemcpyAsync(h->h_pinned, h->d_slab, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        {
+        ClassTimer tm(h, c.st, 3);
         CU(launch_slab_finish(c.A, c.lda, a, col0, w, c.M, h->d_slab, c.st));
+        }
         h->stats.launches += 2;
         CK(sync_stream(h, c.st));
         r1 = h->h_pinned[0];
@@ -370,7 +539,7 @@ cup_status cup_set_option(cup_handle *h, int option, int64_t value)
         h->validate = value != 0;
         return CUP_OK;
     case CUP_OPT_PROFILE:
-        h->profile = value != 0;
+        h->profile = (int)value;
         return CUP_OK;
     default:
         return CUP_ERR_ARG;
@@ -384,11 +553,19 @@ cup_status cup_get_stats(cup_handle *h, cup_stats *out)
     return CUP_OK;
 }
 
+cup_status cup_class_ms(cup_handle *h, double *out8)
+{
+    if (!h || !out8) return CUP_ERR_ARG;
+    for (int i = 0; i < 8; ++i) out8[i] = h->cls_ms[i];
+    return CUP_OK;
+}
+
 cup_status cup_reset_stats(cup_handle *h)
 {
     if (!h) return CUP_ERR_ARG;
     flush_timings(h);
     h->stats = cup_stats{};
+    for (int i = 0; i < 8; ++i) h->cls_ms[i] = 0.0;
     return CUP_OK;
 }
 
@@ -515,25 +692,203 @@ cup_status cup_det(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t 
 
 cup_status cup_inverse(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t p, void *stream)
 {
-    (void)h; (void)A; (void)n; (void)lda; (void)p; (void)stream;
-    return CUP_ERR_UNSUPPORTED;
+    if (!h || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (n == 0) return CUP_OK;
+    if (!A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t *d_idx = nullptr;
+    CU(cudaMalloc(&d_idx, 2 * (size_t)n * sizeof(int64_t)));
+    int64_t r = 0;
+    const ModP M = make_modp(p);
+    cup_status s = cup_factor(h, A, n, n, lda, p, d_idx, d_idx + n, &r, stream);
+    if (s == CUP_OK && r < n) s = CUP_SINGULAR;
+    if (s == CUP_OK) s = red_col_ech(h, A, n, n, lda, r, d_idx, M, h->engine, st);
+    // A^{-1} = P^T X1: row swaps (j, ipiv[j]) for j = n-1 down to 0
+    if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(A, lda, n, d_idx + n, n, 0, 0, 1, 0, st));
+    if (s == CUP_OK) s = check_device_error(h, st);
+    cudaFree(d_idx);
+    return s;
 }
 
 cup_status cup_rref(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
                     int64_t *d_profile, int64_t *rank, uint32_t *X, int64_t ldx, void *stream)
 {
-    (void)h; (void)A; (void)m; (void)n; (void)lda; (void)p; (void)d_profile; (void)rank; (void)X;
-    (void)ldx; (void)stream;
-    return CUP_ERR_UNSUPPORTED;
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    if (X && ldx < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    if (m == 0 || n == 0) {
+        if (X && n > 0) {
+            DeviceGuard g(h->device);
+            CU(launch_fill(X, ldx, n, n, 1, (cudaStream_t)stream));
+            CU(cudaStreamSynchronize((cudaStream_t)stream));
+        }
+        return CUP_OK;
+    }
+    if (!A || !d_profile) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t kmn = m < n ? m : n;
+    int64_t *d_ipiv = nullptr;
+    CU(cudaMalloc(&d_ipiv, (size_t)kmn * sizeof(int64_t)));
+    int64_t r = 0;
+    const ModP M = make_modp(p);
+    cup_status s = cup_factor(h, A, m, n, lda, p, d_profile, d_ipiv, &r, stream);
+    if (s == CUP_OK) s = red_col_ech(h, A, m, n, lda, r, d_profile, M, h->engine, st);
+    if (s == CUP_OK && X) {
+        // X = P^T [X1 X2; 0 I]
+        s = cuda_ok(h, launch_copy(X, ldx, A, lda, r, n, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_fill(X + r * ldx, ldx, n - r, r, 0, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_fill(X + r * ldx + r, ldx, n - r, n - r, 1, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(X, ldx, n, d_ipiv, r, 0, 0, 1, 0, st));
+    }
+    if (s == CUP_OK) {
+        // R = [I_r 0; R2 0] with the profile loop undone (swaps in reverse order)
+        s = cuda_ok(h, launch_fill(A, lda, r, n, 1, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(A, lda, n, d_profile, r, 0, 0, 1, 0, st));
+    }
+    if (s == CUP_OK) s = check_device_error(h, st);
+    if (s == CUP_OK) *rank = r;
+    cudaFree(d_ipiv);
+    return s;
 }
 
 cup_status cup_solve(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t *B,
                      int64_t k, int64_t ldb, uint32_t *X, int64_t ldx, uint32_t p, int64_t *rank,
                      void *stream)
 {
-    (void)h; (void)A; (void)m; (void)n; (void)lda; (void)B; (void)k; (void)ldb; (void)X; (void)ldx;
-    (void)p; (void)rank; (void)stream;
-    return CUP_ERR_UNSUPPORTED;
+    if (!h || !rank || m < 0 || n < 0 || k < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    if (ldb < (k > 0 ? k : 1) || ldx < (k > 0 ? k : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (k == 0) return CUP_OK;
+    if (n > 0 && !X) return CUP_ERR_ARG;
+    if (m == 0 || n == 0) {
+        if (n > 0) CU(launch_fill(X, ldx, n, k, 0, st));
+        int *d_flag = nullptr;
+        CU(cudaMalloc(&d_flag, sizeof(int)));
+        CU(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+        cup_status s = cuda_ok(h, launch_any_nonzero(B, ldb, m, k, d_flag, st));
+        int hf = 0;
+        if (s == CUP_OK) s = cuda_ok(h, cudaMemcpyAsync(&hf, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (s == CUP_OK) s = cuda_ok(h, cudaStreamSynchronize(st));
+        cudaFree(d_flag);
+        if (s == CUP_OK && hf) s = CUP_INCONSISTENT;
+        return s;
+    }
+    if (!A || !B) return CUP_ERR_ARG;
+    const int64_t kmn = m < n ? m : n;
+    const ModP M = make_modp(p);
+    int64_t *d_idx = nullptr;
+    uint32_t *d_L = nullptr, *d_Y = nullptr, *d_C = nullptr;
+    int *d_flag = nullptr;
+    CU(cudaMalloc(&d_idx, 2 * (size_t)kmn * sizeof(int64_t)));
+    int64_t r = 0;
+    cup_status s = cup_factor(h, A, m, n, lda, p, d_idx, d_idx + kmn, &r, stream);
+    const int64_t *d_prof = d_idx, *d_ipiv = d_idx + kmn;
+    const int64_t rr = r > 0 ? r : 1;
+    if (s == CUP_OK) s = cuda_ok(h, cudaMalloc(&d_L, (size_t)rr * rr * sizeof(uint32_t)));
+    if (s == CUP_OK) s = cuda_ok(h, cudaMalloc(&d_Y, (size_t)rr * k * sizeof(uint32_t)));
+    if (s == CUP_OK) s = cuda_ok(h, cudaMalloc(&d_C, (size_t)m * rr * sizeof(uint32_t)));
+    if (s == CUP_OK) s = cuda_ok(h, cudaMalloc(&d_flag, sizeof(int)));
+    if (s == CUP_OK) s = cuda_ok(h, cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+    if (s == CUP_OK && r > 0) {
+        // y1 = L1^{-1} b[profile], L1 = the profile rows of C (lower triangular)
+        s = cuda_ok(h, launch_gather_rows(d_L, r, A, lda, d_prof, r, r, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_gather_rows(d_Y, k, B, ldb, d_prof, r, k, st));
+        if (s == CUP_OK) s = tri_op(h, TRI_LEFT | TRI_SOLVE, d_L, r, d_Y, k, r, k, M, h->engine, st);
+        // consistency: b - C[:, 0:r] y1 must vanish (C without U's part above the diagonal)
+        if (s == CUP_OK) s = cuda_ok(h, launch_copy(d_C, r, A, lda, m, r, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_zero_upper(d_C, r, r, st));
+        if (s == CUP_OK) s = mm_sub(h, B, ldb, d_C, r, d_Y, k, m, k, r, M, h->engine, st, 0);
+        // z1 = U1^{-1} y1
+        if (s == CUP_OK) s = tri_op(h, TRI_LEFT | TRI_UPPER | TRI_UNIT | TRI_SOLVE, A, lda, d_Y, k, r, k, M,
+                                    h->engine, st);
+    }
+    if (s == CUP_OK) s = cuda_ok(h, launch_any_nonzero(B, ldb, m, k, d_flag, st));
+    // x = P^T [z1; 0]
+    if (s == CUP_OK && r > 0) s = cuda_ok(h, launch_copy(X, ldx, d_Y, k, r, k, st));
+    if (s == CUP_OK) s = cuda_ok(h, launch_fill(X + r * ldx, ldx, n - r, k, 0, st));
+    if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(X, ldx, k, d_ipiv, r, 0, 0, 1, 0, st));
+    int hf = 0;
+    if (s == CUP_OK) s = cuda_ok(h, cudaMemcpyAsync(h->h_pinned + 4, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (s == CUP_OK) s = check_device_error(h, st);
+    if (s == CUP_OK) hf = h->h_pinned[4];
+    if (s == CUP_OK) {
+        *rank = r;
+        if (hf) s = CUP_INCONSISTENT;
+    }
+    cudaFree(d_idx);
+    if (d_L) cudaFree(d_L);
+    if (d_Y) cudaFree(d_Y);
+    if (d_C) cudaFree(d_C);
+    if (d_flag) cudaFree(d_flag);
+    return s;
+}
+
+static int tri_flags(int flags, bool solve)
+{
+    return ((flags & CUP_LEFT) ? TRI_LEFT : 0) | ((flags & CUP_UPPER) ? TRI_UPPER : 0) |
+           ((flags & CUP_UNIT) ? TRI_UNIT : 0) | (solve ? TRI_SOLVE : 0);
+}
+
+static cup_status tri_entry(cup_handle *h, int flags, bool solve, const uint32_t *T, int64_t ldt, uint32_t *B,
+                            int64_t ldb, int64_t rows, int64_t cols, uint32_t p, void *stream)
+{
+    if (!h || rows < 0 || cols < 0 || (flags & ~7)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (rows == 0 || cols == 0) return CUP_OK;
+    const int64_t n = (flags & CUP_LEFT) ? rows : cols;
+    if (!T || !B || ldt < n || ldb < cols) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(tri_op(h, tri_flags(flags, solve), T, ldt, B, ldb, rows, cols, make_modp(p), h->engine,
+              (cudaStream_t)stream));
+    CK(check_device_error(h, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+cup_status cup_trsm(cup_handle *h, int flags, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
+                    int64_t rows, int64_t cols, uint32_t p, void *stream)
+{
+    return tri_entry(h, flags, true, T, ldt, B, ldb, rows, cols, p, stream);
+}
+
+cup_status cup_trmm(cup_handle *h, int flags, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
+                    int64_t rows, int64_t cols, uint32_t p, void *stream)
+{
+    return tri_entry(h, flags, false, T, ldt, B, ldb, rows, cols, p, stream);
+}
+
+cup_status cup_trtri(cup_handle *h, int flags, uint32_t *T, int64_t ldt, int64_t n, uint32_t p, void *stream)
+{
+    if (!h || n < 0 || (flags & ~7)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (n == 0) return CUP_OK;
+    if (!T || ldt < n) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(trtri(h, (flags & CUP_UPPER) != 0, (flags & CUP_UNIT) != 0, T, ldt, n, make_modp(p), h->engine,
+             (cudaStream_t)stream));
+    CK(check_device_error(h, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+cup_status cup_trulm(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, uint32_t p, void *stream)
+{
+    if (!h || n < 0) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (n == 0) return CUP_OK;
+    if (!A || lda < n) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(trulm(h, A, lda, n, make_modp(p), h->engine, (cudaStream_t)stream));
+    CK(check_device_error(h, (cudaStream_t)stream));
+    return CUP_OK;
 }
 
 }  // extern "C"

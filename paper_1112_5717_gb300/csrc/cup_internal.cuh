@@ -10,7 +10,8 @@
 #define CUP_QT 64          // column positions per CTA in the leaf finish kernel
 
 // What the leaf pivot kernel hands to the leaf finish kernel (device memory).
-// Positions are relative to the slab's first active column col0.
+// Positions are relative to the slab's first active column col0; rows are
+// relative to the slab's first row.
 struct SlabScratch {
     int r_s;                 // pivots found
     int i_stop;              // rows resolved (the rest need the node update first)
@@ -18,17 +19,21 @@ struct SlabScratch {
     int ext_pos;             // position >= wne that received window column 0, or -1
     int ext_slot;            // slot of ext_pos in Dorig
     int n_slot;
+    int n_spec;              // rows taken as dependent because their window residual vanished
+    int spec_fail;           // set by the finish kernel if such a row has a nonzero residual
+    int spec_rows[CUP_BMAX];
     int prof[CUP_BMAX];      // slab-relative row of pivot t
     int win_col[CUP_WNMAX];  // original position held by window position q
     int win_slot[CUP_WNMAX]; // Dorig slot of window position q, or -1 if not displaced
+    uint32_t pinv[CUP_BMAX];             // 1 / C[prof t][t]
+    uint32_t Linv[CUP_BMAX][CUP_BMAX];   // inverse of L = (C[prof t][u])_{t,u}: U rows = Linv X
     uint32_t Cn[CUP_BMAX][CUP_BMAX];     // C[i][t] for slab rows i < i_stop, t < r_s
-    uint32_t Minv[CUP_BMAX][CUP_BMAX];   // U rows = Minv * (pivot rows of the original slab)
-    uint32_t Dorig[CUP_NSLOT][CUP_BMAX]; // original pivot-row values of displaced positions
+    uint32_t Dorig[CUP_NSLOT][CUP_BMAX]; // original values of displaced positions, per slab row
 };
 
 // Kernel launchers (cup_kernels.cu). All are asynchronous on `st`.
 cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, int64_t col0,
-                               int64_t w, int wn, ModP M, SlabScratch *S, int64_t *ipiv,
+                               int64_t w, int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv,
                                int64_t *prof, cudaStream_t st);
 cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int64_t col0, int64_t w,
                                ModP M, const SlabScratch *S, cudaStream_t st);
@@ -40,7 +45,7 @@ cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, in
                                  int64_t m, int n, ModP M, cudaStream_t st);
 cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                                uint32_t *C, int64_t ldc, int64_t Mr, int64_t N, int64_t K, ModP M,
-                               cudaStream_t st);
+                               cudaStream_t st, int add = 0);
 cudaError_t launch_det_reduce(const uint32_t *A, int64_t lda, int64_t n, const int64_t *ipiv, ModP M,
                               uint32_t *out, cudaStream_t st);
 
@@ -49,4 +54,23 @@ int tc_limbs(uint32_t p);
 size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K);
 cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
-                               cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                               cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                               int add = 0);
+
+// Triangular building blocks (cup_tri.cu). Flags of launch_tri_leaf: the
+// triangle T is n x n with n = rows (left) or cols (right) of B, n <= 64.
+enum { TRI_LEFT = 1, TRI_UPPER = 2, TRI_UNIT = 4, TRI_SOLVE = 8 };
+cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
+                            int64_t rows, int64_t cols, ModP M, cudaStream_t st);
+cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int n, ModP M, cudaStream_t st);
+cudaError_t launch_trulm_leaf(uint32_t *A, int64_t lda, int n, ModP M, cudaStream_t st);
+cudaError_t launch_negate(uint32_t *B, int64_t ldb, int64_t m, int64_t n, uint32_t p, cudaStream_t st);
+cudaError_t launch_row_swaps(uint32_t *A, int64_t lda, int64_t ncols, const int64_t *list, int64_t count,
+                             int64_t base_a, int64_t base_b, int reverse, int prefix, cudaStream_t st);
+cudaError_t launch_gather_rows(uint32_t *dst, int64_t ldd, const uint32_t *src, int64_t lds, const int64_t *idx,
+                               int64_t nrows, int64_t ncols, cudaStream_t st);
+cudaError_t launch_fill(uint32_t *B, int64_t ldb, int64_t m, int64_t n, int diag, cudaStream_t st);
+cudaError_t launch_any_nonzero(const uint32_t *B, int64_t ldb, int64_t m, int64_t n, int *flag, cudaStream_t st);
+cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
+                        cudaStream_t st);
+cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t st);

@@ -33,55 +33,80 @@
 // calls the kernel again on them.
 // ---------------------------------------------------------------------------
 #define PIV_THREADS 512
-#define PIV_LDW (CUP_WNMAX + CUP_BMAX + 1)
+#define PIV_LDW (CUP_WNMAX + 1)
 
+// One fraction-free update f x - m y, scaled by R^{-1} in the Montgomery
+// variant (odd p): the common factor only changes the tracked row scales.
+template <bool MONT>
+__device__ __forceinline__ uint32_t ff(uint32_t f, uint32_t x, uint32_t m, uint32_t y, const ModP &M)
+{
+    return MONT ? ffupd_mont(f, x, m, y, M) : ffupd(f, x, m, y, M);
+}
+
+template <bool MONT>
+__device__ __forceinline__ uint32_t scale_mul(uint32_t a, uint32_t b, const ModP &M)
+{
+    return MONT ? redc((uint64_t)a * b, M) : mulm(a, b, M);
+}
+
+template <bool MONT>
+__device__ __forceinline__ uint32_t inv_any(uint32_t a, const ModP &M)
+{
+    return MONT ? invm_mont(a, M) : invm(a, M);
+}
+
+// First position q in [r, wne) of window row `row` holding a nonzero, or -1.
+// Every warp runs it on the same data, so its result needs no broadcast.
+__device__ __forceinline__ int window_search(const uint32_t *row, int r, int wne, int lane)
+{
+    for (int q0 = r; q0 < wne; q0 += 32) {
+        const int q = q0 + lane;
+        const uint32_t v = (q < wne) ? row[q] : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, v != 0u);
+        if (bal) return q0 + __ffs(bal) - 1;
+    }
+    return -1;
+}
+
+template <bool MONT>
 __global__ void __launch_bounds__(PIV_THREADS)
 k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, int64_t col0,
-              int64_t w, int wn, ModP M, SlabScratch *__restrict__ S, int64_t *__restrict__ g_ipiv,
-              int64_t *__restrict__ g_prof)
+              int64_t w, int wn, int speculate, ModP M, SlabScratch *__restrict__ S,
+              int64_t *__restrict__ g_ipiv, int64_t *__restrict__ g_prof)
 {
-    extern __shared__ uint32_t W[];            // brows x PIV_LDW: window, then T columns
+    extern __shared__ uint32_t W[];            // brows x PIV_LDW window
     __shared__ int s_wcol[CUP_WNMAX];
-    __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX];
-    __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_Sinv[CUP_BMAX], s_Sfwd[CUP_BMAX];
+    __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX], s_spec[CUP_BMAX];
+    __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_muinv[CUP_BMAX], s_Sinv[CUP_BMAX],
+        s_Sfwd[CUP_BMAX];
     __shared__ int s_c, s_ext;
+    __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
 
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int wne = (int)(w < (int64_t)wn ? w : (int64_t)wn);
-    const int TC = CUP_WNMAX;
+    const uint32_t one = 1u % M.p;
 
     for (int idx = tid; idx < brows * wne; idx += nt) {
         int i = idx / wne, q = idx - i * wne;
         W[i * PIV_LDW + q] = A[(a + i) * lda + col0 + q];
     }
-    for (int idx = tid; idx < brows * brows; idx += nt) {
-        int i = idx / brows, j = idx - i * brows;
-        W[i * PIV_LDW + TC + j] = 0u;
-    }
     for (int q = tid; q < wne; q += nt) s_wcol[q] = q;
     if (tid == 0) s_ext = -1;
     __syncthreads();
 
-    int r = 0, stop = brows;
-    uint32_t Sprod = 1u % M.p;                 // product of the pivots f taken so far
+    int r = 0, stop = brows, nspec = 0;
+    uint32_t Sprod = one;                      // product of the row scales applied so far
     for (int i = 0; i < brows; ++i) {
         if ((int64_t)r >= w) break;            // every column is a pivot: later rows are dependent
-        if (warp == 0) {
-            int c = -1;
-            for (int q0 = r; q0 < wne; q0 += 32) {
-                int q = q0 + lane;
-                uint32_t v = (q < wne) ? W[i * PIV_LDW + q] : 0u;
-                unsigned bal = __ballot_sync(0xffffffffu, v != 0u);
-                if (bal) { c = q0 + __ffs(bal) - 1; break; }
-            }
-            if (lane == 0) s_c = c;
-        }
-        __syncthreads();
-        int c = s_c;
-        __syncthreads();
+        int c = window_search(W + i * PIV_LDW, r, wne, lane);
         if (c < 0) {
             if ((int64_t)wne == w) continue;   // whole residual known and zero
-            if (r != 0) { stop = i; break; }
+            if (r != 0) {
+                if (!speculate) { stop = i; break; }
+                if (tid == 0) s_spec[nspec] = i;   // verified by the finish kernel
+                ++nspec;
+                continue;
+            }
             // No pivot yet in this slab: row i of A is still the unreduced,
             // unpermuted input, so its first nonzero beyond the window is read directly.
             if (tid == 0) s_c = INT_MAX;
@@ -108,68 +133,111 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         }
         const uint32_t f = W[i * PIV_LDW + r];
         if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
-        // rows below: window positions (r, wne) and T columns [0, i]; 64 column
-        // slots x (nt / 64) row groups, no index division
-        const int nwin = wne - r - 1;
-        const int ncols = nwin + i + 1;
+        // rows below, window positions (r, wne): one column per thread slot,
+        // the pivot-row entry kept in a register
         {
-            const int cx = tid & 63, ry = tid >> 6, nry = nt >> 6;
-            for (int ii = i + 1 + ry; ii < brows; ii += nry) {
-                uint32_t *wr = W + ii * PIV_LDW;
-                const uint32_t m = wr[r];
-                for (int j = cx; j < ncols; j += 64) {
-                    if (j < nwin) {
-                        const int q = r + 1 + j;
-                        wr[q] = ffupd(f, wr[q], m, W[i * PIV_LDW + q], M);
-                    } else {
-                        const int jj = j - nwin;   // T column jj <= i; T[i][i] is the product Sprod
-                        const uint32_t y = (jj == i) ? Sprod : W[i * PIV_LDW + TC + jj];
-                        wr[TC + jj] = ffupd(f, wr[TC + jj], m, y, M);
-                    }
+            const int nq = wne - r - 1;
+            const int cx = tid & 127, ry = tid >> 7, nry = nt >> 7;
+            if (cx < nq) {
+                const int q = r + 1 + cx;
+                const uint32_t y = W[i * PIV_LDW + q];
+                for (int ii = i + 1 + ry; ii < brows; ii += nry) {
+                    uint32_t *wr = W + ii * PIV_LDW;
+                    wr[q] = ff<MONT>(f, wr[q], wr[r], y, M);
                 }
             }
         }
         __syncthreads();
-        Sprod = mulm(Sprod, f, M);
+        Sprod = scale_mul<MONT>(Sprod, f, M);
         ++r;
     }
     const int rs = r;
 
-    for (int t = tid; t < rs; t += nt) s_finv[t] = invm(s_f[t], M);
+    // Row scale of step t: mu_t = f_t (R^{-1} f_t in the Montgomery variant).
+    for (int t = tid; t < rs; t += nt) {
+        const uint32_t mu = MONT ? redc((uint64_t)s_f[t], M) : s_f[t];
+        const uint32_t muinv = inv_any<MONT>(mu, M);
+        s_muinv[t] = muinv;
+        s_finv[t] = MONT ? redc((uint64_t)muinv, M) : muinv;   // f^{-1} = mu^{-1} R^{-1}
+    }
     __syncthreads();
     if (warp == 0) {
-        // exclusive prefix products Sinv[t] = prod_{t' < t} finv[t'] (two 32-element scans)
-        uint32_t carry = 1u % M.p;
+        // exclusive prefix products Sinv[t] = prod_{t' < t} mu_{t'}^{-1}
+        uint32_t carry = one;
         for (int base = 0; base < rs; base += 32) {
             const int t = base + lane;
-            uint32_t v = (t < rs) ? s_finv[t] : 1u % M.p;
+            uint32_t v = (t < rs) ? s_muinv[t] : one;
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v = mulm(v, u, M);
             }
             uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
-            if (lane == 0) ex = 1u % M.p;
+            if (lane == 0) ex = one;
             if (t < rs) s_Sinv[t] = mulm(carry, ex, M);
             carry = mulm(carry, __shfl_sync(0xffffffffu, v, 31), M);
         }
     }
     __syncthreads();
 
-    // C values of the resolved rows: W[i][t] carries the scale prod_{t'<t} f_{t'}
+    // C values of the resolved rows: W[i][t] carries the scale S_t of step t;
+    // the pivot itself is f_t / S_t, so its inverse is S_t / f_t
     for (int idx = tid; idx < stop * rs; idx += nt) {
         int i = idx / rs, t = idx - i * rs;
         uint32_t v = (i >= s_prof[t]) ? mulm(W[i * PIV_LDW + t], s_Sinv[t], M) : 0u;
         S->Cn[i][t] = v;
     }
-    // Minv[t][t'] = T[prof t][prof t'] / f_t, with T's diagonal entry the scale of row prof t
-    for (int idx = tid; idx < rs * rs; idx += nt) {
-        int t = idx / rs, u = idx - t * rs;
-        uint32_t v = 0u;
-        if (u < t) v = mulm(W[s_prof[t] * PIV_LDW + TC + s_prof[u]], s_finv[t], M);
-        else if (u == t) v = mulm(s_Sfwd[t], s_finv[t], M);
-        S->Minv[t][u] = v;
+    __syncthreads();
+    // L^{-1} for the finish kernel, L[t][u] = C[prof t][u] (lower triangular,
+    // pivots on the diagonal), by merging inverted diagonal blocks:
+    // inv([L11 0; L21 L22]) = [inv(L11) 0; -inv(L22) L21 inv(L11), inv(L22)].
+    // The window W is free now; it holds L (cols 0..63), Linv (64..127) and a temporary.
+    {
+        uint32_t *sL = W;                                  // rs x rs, row stride PIV_LDW
+        uint32_t *sI = W + CUP_BMAX;                       // Linv, same rows, columns offset by 64
+        uint32_t *sT = W + (size_t)CUP_BMAX * PIV_LDW;     // temporary, only if brows > ... (see launcher)
+        for (int idx = tid; idx < rs * rs; idx += nt) {
+            const int t = idx / rs, u = idx - t * rs;
+            const uint32_t c = (u <= t) ? mulm(W[s_prof[t] * PIV_LDW + u], s_Sinv[u], M) : 0u;
+            sT[t * CUP_BMAX + u] = c;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < rs * rs; idx += nt) {
+            const int t = idx / rs, u = idx - t * rs;
+            sL[t * PIV_LDW + u] = sT[t * CUP_BMAX + u];
+            sI[t * PIV_LDW + u] = (u == t) ? mulm(s_Sfwd[t], s_finv[t], M) : 0u;
+        }
+        __syncthreads();
+        for (int sz = 1; sz < rs; sz *= 2) {
+            // T = L21 inv(L11) for every block pair at this level
+            for (int idx = tid; idx < rs * sz; idx += nt) {
+                const int t = idx / sz, uu = idx - t * sz;          // row t, column b0 + uu
+                const int b0 = (t / (2 * sz)) * (2 * sz);
+                if (t < b0 + sz) continue;                          // rows of the top block
+                const int u = b0 + uu;
+                Acc acc = {0ull, 0u};
+                for (int v = u; v < b0 + sz; ++v) acc_add(acc, (uint64_t)sL[t * PIV_LDW + v] * sI[v * PIV_LDW + u]);
+                sT[t * CUP_BMAX + u] = acc_red(acc, M);
+            }
+            __syncthreads();
+            // X21 = -inv(L22) T
+            for (int idx = tid; idx < rs * sz; idx += nt) {
+                const int t = idx / sz, uu = idx - t * sz;
+                const int b0 = (t / (2 * sz)) * (2 * sz);
+                if (t < b0 + sz) continue;
+                const int u = b0 + uu;
+                Acc acc = {0ull, 0u};
+                for (int v = b0 + sz; v <= t; ++v) acc_add(acc, (uint64_t)sI[t * PIV_LDW + v] * sT[v * CUP_BMAX + u]);
+                const uint32_t x = acc_red(acc, M);
+                sI[t * PIV_LDW + u] = x ? M.p - x : 0u;
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < rs * rs; idx += nt) {
+            const int t = idx / rs, u = idx - t * rs;
+            S->Linv[t][u] = sI[t * PIV_LDW + u];
+        }
     }
-    __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
+    for (int t = tid; t < rs; t += nt) S->pinv[t] = mulm(s_Sfwd[t], s_finv[t], M);
     if (warp == 0) {
         int ns = 0;
         for (int base = 0; base < wne; base += 32) {
@@ -193,6 +261,8 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
             S->r_s = rs;
             S->i_stop = stop;
             S->wne = wne;
+            S->n_spec = nspec;
+            S->spec_fail = 0;
         }
     }
     for (int t = tid; t < rs; t += nt) {
@@ -200,65 +270,134 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         g_ipiv[col0 + t] = col0 + s_pos[t];
         g_prof[col0 + t] = a + s_prof[t];
     }
+    for (int k = tid; k < nspec; k += nt) S->spec_rows[k] = s_spec[k];
     __syncthreads();
-    // original pivot-row values of every displaced position
+    // original values of every displaced position, for every slab row
     const int nslot = s_slot[0];
-    for (int idx = tid; idx < nslot * rs; idx += nt) {
-        int sl = idx / rs, t = idx - sl * rs;
-        S->Dorig[sl][t] = A[(a + s_prof[t]) * lda + col0 + s_sorig[sl]];
+    for (int idx = tid; idx < nslot * brows; idx += nt) {
+        int sl = idx / brows, i = idx - sl * brows;
+        S->Dorig[sl][i] = A[(a + i) * lda + col0 + s_sorig[sl]];
     }
 }
 
 // ---------------------------------------------------------------------------
 // Leaf slab, finish phase (grid over column positions).
 //
-// For each position q of the slab: U's rows at q are Minv times the original
-// pivot-row values of the column now at q (via the recorded transpositions);
-// the final [C\U] content is then written with U's rows placed directly at
-// global rows col0 .. col0 + r_s (their place in the space-sharing storage of
-// the whole matrix) and C in the slab rows.
+// For each position q of the slab, U's rows at q solve L u = x, with x the
+// original pivot-row values of the column now at q (via the recorded
+// transpositions) and L the pivot rows of C (lower triangular, pivots on the
+// diagonal): a forward substitution done by four lanes per column. The final
+// [C\U] content is then written with U's rows placed directly at global rows
+// col0 .. col0 + r_s (their place in the space-sharing storage of the whole
+// matrix) and C in the slab rows. Rows taken as dependent by a speculating
+// pivot kernel are checked here: their residual x - C u must vanish.
 // ---------------------------------------------------------------------------
+template <bool WIDE>
 __global__ void __launch_bounds__(256)
 k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int64_t col0, int64_t w, ModP M,
-              const SlabScratch *__restrict__ S)
+              SlabScratch *__restrict__ S)
 {
-    __shared__ uint32_t sMinv[CUP_BMAX][CUP_BMAX + 1];
-    __shared__ uint32_t sX[CUP_BMAX][CUP_QT];
-    __shared__ uint32_t sU[CUP_BMAX][CUP_QT];
+    __shared__ uint32_t sL[CUP_BMAX][CUP_BMAX + 1];
+    __shared__ uint32_t sX[CUP_BMAX][CUP_QT + 1];
+    __shared__ uint32_t sPinv[CUP_BMAX];
     __shared__ int sOrig[CUP_QT], sSlot[CUP_QT], sProf[CUP_BMAX];
 
     const int rs = S->r_s, stop = S->i_stop, wne = S->wne;
     const int64_t q0 = (int64_t)blockIdx.x * CUP_QT;
     if (q0 >= w) return;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
+    const int ext_pos = S->ext_pos, ext_slot = S->ext_slot;
 
-    for (int idx = tid; idx < rs * rs; idx += nt) {
-        int t = idx / rs, u = idx - t * rs;
-        sMinv[t][u] = S->Minv[t][u];
-    }
-    for (int t = tid; t < rs; t += nt) sProf[t] = S->prof[t];
+    for (int t = tid; t < rs; t += nt) { sProf[t] = S->prof[t]; sPinv[t] = S->pinv[t]; }
     for (int qq = tid; qq < nq; qq += nt) {
         int64_t q = q0 + qq;
         int orig, slot;
         if (q < wne) { orig = S->win_col[q]; slot = S->win_slot[q]; }
-        else if (q == S->ext_pos) { orig = 0; slot = S->ext_slot; }
+        else if (q == ext_pos) { orig = 0; slot = ext_slot; }
         else { orig = (int)q; slot = -1; }
         sOrig[qq] = orig;
         sSlot[qq] = slot;
     }
     __syncthreads();
-    for (int idx = tid; idx < rs * nq; idx += nt) {
-        int t = idx / nq, qq = idx - t * nq;
-        int slot = sSlot[qq];
-        sX[t][qq] = (slot >= 0) ? S->Dorig[slot][t] : A[(a + sProf[t]) * lda + col0 + sOrig[qq]];
+    for (int idx = tid; idx < CUP_BMAX * CUP_BMAX; idx += nt) {
+        int t = idx / CUP_BMAX, u = idx - t * CUP_BMAX;
+        sL[t][u] = (t < rs && u < rs) ? S->Linv[t][u] : 0u;
+    }
+    for (int idx = tid; idx < CUP_BMAX * CUP_QT; idx += nt) {
+        int t = idx / CUP_QT, qq = idx - t * CUP_QT;
+        uint32_t v = 0u;
+        if (t < rs && qq < nq) {
+            int slot = sSlot[qq];
+            v = (slot >= 0) ? S->Dorig[slot][sProf[t]] : A[(a + sProf[t]) * lda + col0 + sOrig[qq]];
+        }
+        sX[t][qq] = v;
     }
     __syncthreads();
-    for (int idx = tid; idx < rs * nq; idx += nt) {
-        int t = idx / nq, qq = idx - t * nq;
-        Acc acc = {0ull, 0u};
-        for (int u = 0; u <= t; ++u) acc_add(acc, (uint64_t)sMinv[t][u] * sX[u][qq]);
-        sU[t][qq] = acc_red(acc, M);
+    // U tile = Linv X: each thread a 4 x 4 block (rows ty + 16 i, columns tx + 16 j)
+    {
+        const int tx = tid & 15, ty = tid >> 4;
+        uint64_t lo[4][4];
+        uint32_t hi[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { lo[i][j] = 0ull; hi[i][j] = 0u; }
+        for (int u = 0; u < rs; ++u) {
+            uint32_t av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = sL[ty + 16 * i][u];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = sX[u][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t pr = (uint64_t)av[i] * bv[j];
+                    if (WIDE) {
+                        const uint64_t s2 = lo[i][j] + pr;
+                        hi[i][j] += (s2 < pr);
+                        lo[i][j] = s2;
+                    } else {
+                        lo[i][j] += pr;
+                    }
+                }
+        }
+        __syncthreads();                                   // every read of sX is done
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = ty + 16 * i;
+                if (t < rs) {
+                    Acc acc = {lo[i][j], hi[i][j]};
+                    sX[t][tx + 16 * j] = acc_red(acc, M);
+                }
+            }
+    }
+    __syncthreads();
+    // rows taken as dependent: residual x_i - sum_t C[i][t] u_t must be zero at every position
+    const int nspec = S->n_spec;
+    if (nspec > 0) {
+        int bad = 0;
+        for (int idx = tid; idx < nspec * nq; idx += nt) {
+            const int k = idx / nq, qq = idx - k * nq;
+            const int i = S->spec_rows[k];
+            const int slot = sSlot[qq];
+            const uint32_t x = (slot >= 0) ? S->Dorig[slot][i] : A[(a + i) * lda + col0 + sOrig[qq]];
+            Acc acc = {0ull, 0u};
+            for (int t = 0; t < rs; ++t) acc_add(acc, (uint64_t)S->Cn[i][t] * sX[t][qq]);
+            if (acc_red(acc, M) != x) bad = 1;
+        }
+        if (__syncthreads_or(bad) && tid == 0) atomicExch(&S->spec_fail, 1);
+    }
+    // C values for the first tile (positions < r_s <= CUP_QT): sL is free again
+    if (q0 == 0) {
+        __syncthreads();
+        for (int idx = tid; idx < stop * rs; idx += nt) {
+            int i = idx / rs, t = idx - i * rs;
+            sL[i][t] = S->Cn[i][t];
+        }
     }
     __syncthreads();
     // rows: U rows col0 + t (t < rs), then slab rows a + i (i < stop) that are not U rows
@@ -270,14 +409,14 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int64_t col0, in
         uint32_t v;
         if (k < rs) {
             rho = col0 + k;
-            if (q > k) v = sU[k][qq];
-            else if (rho >= a) v = (q < rs) ? S->Cn[rho - a][q] : 0u;
+            if (q > k) v = sX[k][qq];
+            else if (rho >= a) v = (q < rs) ? sL[rho - a][q] : 0u;
             else v = 0u;
         } else {
             int i = k - rs;
             rho = a + i;
             if (rho < col0 + rs) continue;     // written above as a U row
-            v = (q < rs) ? S->Cn[i][q] : 0u;
+            v = (q < rs) ? sL[i][q] : 0u;
         }
         A[rho * lda + col0 + q] = v;
     }
@@ -359,14 +498,17 @@ k_laswp(uint32_t *__restrict__ A, int64_t lda, int64_t row0, int64_t nrows,
 // ---------------------------------------------------------------------------
 #define TRSM_LEAF 64
 #define TRSM_WARPS 8
+template <bool MONT>
 __global__ void __launch_bounds__(32 * TRSM_WARPS)
 k_trsm_ruu_leaf(const uint32_t *__restrict__ U, int64_t ldu, uint32_t *__restrict__ B, int64_t ldb,
                 int64_t m, int n, ModP M)
 {
+    // U in Montgomery form (u R mod p) when p is odd, so that redc(x u R) = x u
     __shared__ uint32_t sU[TRSM_LEAF][TRSM_LEAF];
     for (int idx = threadIdx.x; idx < TRSM_LEAF * TRSM_LEAF; idx += blockDim.x) {
         int k = idx / TRSM_LEAF, j = idx - k * TRSM_LEAF;
-        sU[k][j] = (j > k && j < n && k < n) ? U[k * ldu + j] : 0u;
+        uint32_t u = (j > k && j < n && k < n) ? U[k * ldu + j] : 0u;
+        sU[k][j] = MONT ? redc((uint64_t)u * M.r2, M) : u;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -378,8 +520,13 @@ k_trsm_ruu_leaf(const uint32_t *__restrict__ U, int64_t ldu, uint32_t *__restric
         for (int k = 0; k < n; ++k) {
             const uint32_t xk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
             if (xk) {
-                x0 = subm(x0, mulm(xk, sU[k][lane], M), M);
-                x1 = subm(x1, mulm(xk, sU[k][lane + 32], M), M);
+                if (MONT) {
+                    x0 = subm(x0, redc((uint64_t)xk * sU[k][lane], M), M);
+                    x1 = subm(x1, redc((uint64_t)xk * sU[k][lane + 32], M), M);
+                } else {
+                    x0 = subm(x0, mulm(xk, sU[k][lane], M), M);
+                    x1 = subm(x1, mulm(xk, sU[k][lane + 32], M), M);
+                }
             }
         }
         if (lane < n) row[lane] = x0;
@@ -399,7 +546,7 @@ template <bool WIDE>
 __global__ void __launch_bounds__(256)
 k_gemm_sub_cc(const uint32_t *__restrict__ A, int64_t lda, const uint32_t *__restrict__ B,
               int64_t ldb, uint32_t *__restrict__ C, int64_t ldc, int64_t Mr, int64_t N, int64_t K,
-              ModP Mp)
+              ModP Mp, int add)
 {
     __shared__ uint32_t As[GB_K][GB_M + 4];
     __shared__ uint32_t Bs[GB_K][GB_N + 4];
@@ -456,7 +603,7 @@ k_gemm_sub_cc(const uint32_t *__restrict__ A, int64_t lda, const uint32_t *__res
                 Acc a = {acc[i][j], hi[i][j]};
                 uint32_t v = acc_red(a, Mp);
                 uint32_t *cp = C + gr * ldc + gc;
-                *cp = subm(*cp, v, Mp);
+                *cp = add ? addm(*cp, v, Mp) : subm(*cp, v, Mp);
             }
         }
 }
@@ -465,18 +612,25 @@ k_gemm_sub_cc(const uint32_t *__restrict__ A, int64_t lda, const uint32_t *__res
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, int64_t col0,
-                               int64_t w, int wn, ModP M, SlabScratch *S, int64_t *ipiv,
+                               int64_t w, int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv,
                                int64_t *prof, cudaStream_t st)
 {
     static bool attr = false;
-    size_t smem = (size_t)brows * PIV_LDW * sizeof(uint32_t);
+    // window rows, then a CUP_BMAX^2 temporary used when inverting L
+    const size_t smem = ((size_t)CUP_BMAX * PIV_LDW + (size_t)CUP_BMAX * CUP_BMAX) * sizeof(uint32_t);
+    (void)brows;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_slab_pivots, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(CUP_BMAX * PIV_LDW * sizeof(uint32_t)));
+        const int mx = (int)smem;
+        cudaError_t e = cudaFuncSetAttribute(k_slab_pivots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_slab_pivots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_slab_pivots<<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, w, wn, M, S, ipiv, prof);
+    if (M.p & 1u)
+        k_slab_pivots<true><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, w, wn, speculate, M, S, ipiv, prof);
+    else
+        k_slab_pivots<false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, w, wn, speculate, M, S, ipiv, prof);
     return cudaGetLastError();
 }
 
@@ -485,7 +639,11 @@ cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int64_t col0
 {
     int64_t nb = (w + CUP_QT - 1) / CUP_QT;
     if (nb <= 0) return cudaSuccess;
-    k_slab_finish<<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, w, M, S);
+    // CUP_BMAX (p-1)^2 < 2^64 means a row of Minv times a column of X cannot wrap
+    // a row of Linv times a column of X sums CUP_BMAX products
+    const bool wide = (long double)CUP_BMAX * (M.p - 1) * (long double)(M.p - 1) >= 18446744073709551615.0L;
+    if (wide) k_slab_finish<true><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, w, M, const_cast<SlabScratch *>(S));
+    else k_slab_finish<false><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, w, M, const_cast<SlabScratch *>(S));
     return cudaGetLastError();
 }
 
@@ -512,13 +670,14 @@ cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, in
     if (n > TRSM_LEAF) return cudaErrorInvalidValue;
     int64_t nb = (m + TRSM_WARPS - 1) / TRSM_WARPS;
     if (nb > 152 * 16) nb = 152 * 16;
-    k_trsm_ruu_leaf<<<(unsigned)nb, 32 * TRSM_WARPS, 0, st>>>(U, ldu, B, ldb, m, n, M);
+    if (M.p & 1u) k_trsm_ruu_leaf<true><<<(unsigned)nb, 32 * TRSM_WARPS, 0, st>>>(U, ldu, B, ldb, m, n, M);
+    else k_trsm_ruu_leaf<false><<<(unsigned)nb, 32 * TRSM_WARPS, 0, st>>>(U, ldu, B, ldb, m, n, M);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                                uint32_t *C, int64_t ldc, int64_t Mr, int64_t N, int64_t K, ModP M,
-                               cudaStream_t st)
+                               cudaStream_t st, int add)
 {
     if (Mr <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     dim3 grid((unsigned)((N + GB_N - 1) / GB_N), (unsigned)((Mr + GB_M - 1) / GB_M));
@@ -526,9 +685,9 @@ cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B
     // K (p-1)^2 < 2^64 means the 64-bit sum of products cannot wrap
     long double bound = (long double)K * (long double)(M.p - 1) * (long double)(M.p - 1);
     if (bound < 18446744073709551615.0L)
-        k_gemm_sub_cc<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M);
+        k_gemm_sub_cc<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M, add);
     else
-        k_gemm_sub_cc<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M);
+        k_gemm_sub_cc<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M, add);
     return cudaGetLastError();
 }
 

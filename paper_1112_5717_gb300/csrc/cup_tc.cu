@@ -169,7 +169,7 @@ template <int L>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             uint32_t *__restrict__ C, int64_t ldc, int M, int N, int Kp, ModP Mp, uint64_t off,
-            uint32_t sh32, int *__restrict__ err)
+            uint32_t sh32, int *__restrict__ err, int add)
 {
     using CF = Cfg<L>;
     constexpr int BN = CF::BN, NACC = CF::NACC, NSTAGE = CF::NSTAGE;
@@ -316,7 +316,7 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
             for (int e = 0; e < CPW; ++e) {
                 const int gc = n0 + hcol * CPW + e;
-                if (gc < N) crow[gc] = subm(crow[gc], run[e], Mp);
+                if (gc < N) crow[gc] = add ? addm(crow[gc], run[e], Mp) : subm(crow[gc], run[e], Mp);
             }
         }
     }
@@ -431,7 +431,7 @@ bool make_map(CUtensorMap *map, void *base, int kp, int rows, int L, int box_row
 template <int L>
 cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C, int64_t ldc,
                 int M, int N, int K, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0,
-                cudaEvent_t ev1)
+                cudaEvent_t ev1, int add)
 {
     using CF = Cfg<L>;
     const int Kp = (K + BK - 1) / BK * BK;
@@ -458,7 +458,7 @@ cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, 
     const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
     dim3 grid((N + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
     if (ev0) cudaEventRecord(ev0, st);
-    k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, C, ldc, M, N, Kp, Mp, off, sh32, err);
+    k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, C, ldc, M, N, Kp, Mp, off, sh32, err, add);
     cudaError_t e = cudaGetLastError();
     if (ev1) cudaEventRecord(ev1, st);
     return e;
@@ -483,14 +483,14 @@ size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K)
 
 cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
-                               cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
+                               cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, int add)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2) return cudaErrorInvalidValue;
     switch (tc_limbs(Mp.p)) {
-    case 1: return tc::run<1>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
-    case 2: return tc::run<2>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
-    case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
-    default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1);
+    case 1: return tc::run<1>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
+    case 2: return tc::run<2>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
+    case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
+    default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
     }
 }

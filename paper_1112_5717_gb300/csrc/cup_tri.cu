@@ -1,0 +1,432 @@
+// Triangular building blocks of Sec. 3.2 at their base (blocks of at most 64),
+// plus the small data-movement kernels the derived problems need.
+//
+// k_tri_right: B <- B T^{-1} or B <- B T   (one warp per row of B)
+// k_tri_left:  B <- T^{-1} B or B <- T B   (one thread per column of B)
+// with T upper or lower, unit or non-unit diagonal. The recursive drivers in
+// cup_api.cu split larger triangles in halves and hand the off-diagonal
+// products to the Schur-update engine (Algorithm 2 and its variants, TRMM,
+// Algorithm 3 TRTRI, Algorithm 4 TRULM).
+#include "cup_internal.cuh"
+
+#define TRI_MAX 64
+
+template <bool MONT>
+__device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t bm, const ModP &M)
+{
+    // bm is in Montgomery form (b R mod p) when MONT
+    return MONT ? redc((uint64_t)a * bm, M) : mulm(a, bm, M);
+}
+
+template <bool MONT>
+__device__ __forceinline__ uint32_t to_mont(uint32_t b, const ModP &M)
+{
+    return MONT ? redc((uint64_t)b * M.r2, M) : b;
+}
+
+// Load the n x n triangle (only the triangle that is read) and its diagonal:
+// sD[k] = 1 for unit, T[k][k] for multiply, T[k][k]^{-1} for solve.
+template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
+__device__ void load_tri(const uint32_t *T, int64_t ldt, int n, const ModP &M,
+                         uint32_t (*sT)[TRI_MAX + 1], uint32_t *sD)
+{
+    for (int idx = threadIdx.x; idx < TRI_MAX * TRI_MAX; idx += blockDim.x) {
+        const int k = idx / TRI_MAX, j = idx - k * TRI_MAX;
+        const bool in = (k < n && j < n) && (UPPER ? (j > k) : (j < k));
+        sT[k][j] = to_mont<MONT>(in ? T[k * ldt + j] : 0u, M);
+    }
+    for (int k = threadIdx.x; k < TRI_MAX; k += blockDim.x) {
+        uint32_t d = 1u % M.p;
+        if (!UNIT && k < n) {
+            d = T[k * ldt + k];
+            if (SOLVE) d = invm(d, M);
+        }
+        sD[k] = to_mont<MONT>(d, M);
+    }
+}
+
+template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
+__global__ void __launch_bounds__(256)
+k_tri_right(const uint32_t *__restrict__ T, int64_t ldt, uint32_t *__restrict__ B, int64_t ldb, int64_t m,
+            int n, ModP M)
+{
+    __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
+    __shared__ uint32_t sD[TRI_MAX];
+    load_tri<UPPER, UNIT, SOLVE, MONT>(T, ldt, n, M, sT, sD);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nw) {
+        uint32_t *row = B + i * ldb;
+        uint32_t x0 = (lane < n) ? row[lane] : 0u;
+        uint32_t x1 = (lane + 32 < n) ? row[lane + 32] : 0u;
+        if (SOLVE) {
+            // X T = B: columns in dependency order, each finalised then broadcast
+            for (int s = 0; s < n; ++s) {
+                const int k = UPPER ? s : n - 1 - s;
+                if (!UNIT) {
+                    if (lane == (k & 31)) {
+                        if (k < 32) x0 = mmul<MONT>(x0, sD[k], M);
+                        else x1 = mmul<MONT>(x1, sD[k], M);
+                    }
+                }
+                const uint32_t xk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
+                if (xk) {
+                    x0 = subm(x0, mmul<MONT>(xk, sT[k][lane], M), M);
+                    x1 = subm(x1, mmul<MONT>(xk, sT[k][lane + 32], M), M);
+                }
+            }
+        } else {
+            // Y = B T: y_j = sum_k b_k t_kj over the triangle, plus the diagonal
+            uint32_t y0 = mmul<MONT>(x0, sD[lane], M), y1 = mmul<MONT>(x1, sD[lane + 32], M);
+            for (int k = 0; k < n; ++k) {
+                const uint32_t xk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
+                if (xk) {
+                    y0 = addm(y0, mmul<MONT>(xk, sT[k][lane], M), M);
+                    y1 = addm(y1, mmul<MONT>(xk, sT[k][lane + 32], M), M);
+                }
+            }
+            x0 = y0;
+            x1 = y1;
+        }
+        if (lane < n) row[lane] = x0;
+        if (lane + 32 < n) row[lane + 32] = x1;
+    }
+}
+
+#define TRI_COLS 64
+template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
+__global__ void __launch_bounds__(TRI_COLS)
+k_tri_left(const uint32_t *__restrict__ T, int64_t ldt, uint32_t *__restrict__ B, int64_t ldb, int n,
+           int64_t k, ModP M)
+{
+    __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
+    __shared__ uint32_t sD[TRI_MAX];
+    __shared__ uint32_t sB[TRI_MAX][TRI_COLS];
+    load_tri<UPPER, UNIT, SOLVE, MONT>(T, ldt, n, M, sT, sD);
+    const int c = threadIdx.x;
+    const int64_t col = (int64_t)blockIdx.x * TRI_COLS + c;
+    for (int i = 0; i < n; ++i) sB[i][c] = (col < k) ? B[i * ldb + col] : 0u;
+    __syncthreads();
+    if (col >= k) return;
+    if (SOLVE) {
+        // T X = B: rows in dependency order
+        for (int s = 0; s < n; ++s) {
+            const int i = UPPER ? n - 1 - s : s;
+            uint32_t acc = sB[i][c];
+            if (UPPER) {
+                for (int j = i + 1; j < n; ++j) acc = subm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
+            } else {
+                for (int j = 0; j < i; ++j) acc = subm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
+            }
+            sB[i][c] = mmul<MONT>(acc, sD[i], M);
+        }
+    } else {
+        // Y = T B; rows are overwritten in an order that keeps the inputs they need
+        for (int s = 0; s < n; ++s) {
+            const int i = UPPER ? s : n - 1 - s;
+            uint32_t acc = mmul<MONT>(sB[i][c], sD[i], M);
+            if (UPPER) {
+                for (int j = i + 1; j < n; ++j) acc = addm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
+            } else {
+                for (int j = 0; j < i; ++j) acc = addm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
+            }
+            sB[i][c] = acc;
+        }
+    }
+    for (int i = 0; i < n; ++i) B[i * ldb + col] = sB[i][c];
+}
+
+template <bool UPPER, bool UNIT, bool SOLVE>
+static cudaError_t tri_dispatch(bool left, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
+                                int64_t rows, int64_t cols, int n, ModP M, cudaStream_t st)
+{
+    const bool mont = (M.p & 1u) != 0;
+    if (left) {
+        const int64_t nb = (cols + TRI_COLS - 1) / TRI_COLS;
+        if (mont) k_tri_left<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, TRI_COLS, 0, st>>>(T, ldt, B, ldb, n, cols, M);
+        else k_tri_left<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, TRI_COLS, 0, st>>>(T, ldt, B, ldb, n, cols, M);
+    } else {
+        int64_t nb = (rows + 7) / 8;
+        if (nb > 152 * 16) nb = 152 * 16;
+        if (mont) k_tri_right<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, rows, n, M);
+        else k_tri_right<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, rows, n, M);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
+                            int64_t rows, int64_t cols, ModP M, cudaStream_t st)
+{
+    const bool left = flags & TRI_LEFT, upper = flags & TRI_UPPER, unit = flags & TRI_UNIT,
+               solve = flags & TRI_SOLVE;
+    const int n = (int)(left ? rows : cols);
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (n > TRI_MAX) return cudaErrorInvalidValue;
+    if (upper) {
+        if (unit) return solve ? tri_dispatch<true, true, true>(left, T, ldt, B, ldb, rows, cols, n, M, st)
+                               : tri_dispatch<true, true, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
+        return solve ? tri_dispatch<true, false, true>(left, T, ldt, B, ldb, rows, cols, n, M, st)
+                     : tri_dispatch<true, false, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
+    }
+    if (unit) return solve ? tri_dispatch<false, true, true>(left, T, ldt, B, ldb, rows, cols, n, M, st)
+                           : tri_dispatch<false, true, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
+    return solve ? tri_dispatch<false, false, true>(left, T, ldt, B, ldb, rows, cols, n, M, st)
+                 : tri_dispatch<false, false, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
+}
+
+// ---------------------------------------------------------------------------
+// Small data-movement kernels
+// ---------------------------------------------------------------------------
+__global__ void k_negate(uint32_t *__restrict__ B, int64_t ldb, int64_t m, int64_t n, uint32_t p)
+{
+    const int64_t total = m * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx - i * n;
+        const uint32_t v = B[i * ldb + j];
+        B[i * ldb + j] = v ? p - v : 0u;
+    }
+}
+
+cudaError_t launch_negate(uint32_t *B, int64_t ldb, int64_t m, int64_t n, uint32_t p, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m * n + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_negate<<<(unsigned)nb, 256, 0, st>>>(B, ldb, m, n, p);
+    return cudaGetLastError();
+}
+
+// Row transpositions (rows a_t and b_t swapped for t in order; if reverse, in
+// reverse order): one thread per column, so each column sees the sequence in
+// order. With `prefix`, swap t only touches columns 0..a_t (Algorithm 8's
+// loop, where row j and row i_j exchange their first j + 1 entries).
+// Pair t is (t + base_a, list[t] + base_b) for t in [0, count).
+__global__ void k_row_swaps(uint32_t *__restrict__ A, int64_t lda, int64_t ncols,
+                            const int64_t *__restrict__ list, int64_t count, int64_t base_a,
+                            int64_t base_b, int reverse, int prefix)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    for (int64_t s = 0; s < count; ++s) {
+        const int64_t t = reverse ? count - 1 - s : s;
+        const int64_t ra = t + base_a, rb = list[t] + base_b;
+        if (ra == rb) continue;
+        if (prefix && c > t) continue;
+        const uint32_t x = A[ra * lda + c];
+        A[ra * lda + c] = A[rb * lda + c];
+        A[rb * lda + c] = x;
+    }
+}
+
+cudaError_t launch_row_swaps(uint32_t *A, int64_t lda, int64_t ncols, const int64_t *list, int64_t count,
+                             int64_t base_a, int64_t base_b, int reverse, int prefix, cudaStream_t st)
+{
+    if (ncols <= 0 || count <= 0) return cudaSuccess;
+    k_row_swaps<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(A, lda, ncols, list, count, base_a, base_b,
+                                                                   reverse, prefix);
+    return cudaGetLastError();
+}
+
+// dst[t][0:ncols) = src[idx[t]][0:ncols) for t < nrows
+__global__ void k_gather_rows(uint32_t *__restrict__ dst, int64_t ldd, const uint32_t *__restrict__ src,
+                              int64_t lds, const int64_t *__restrict__ idx, int64_t nrows, int64_t ncols)
+{
+    const int64_t t = blockIdx.y;
+    if (t >= nrows) return;
+    const uint32_t *s = src + idx[t] * lds;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += (int64_t)gridDim.x * blockDim.x)
+        dst[t * ldd + c] = s[c];
+}
+
+cudaError_t launch_gather_rows(uint32_t *dst, int64_t ldd, const uint32_t *src, int64_t lds, const int64_t *idx,
+                               int64_t nrows, int64_t ncols, cudaStream_t st)
+{
+    if (nrows <= 0 || ncols <= 0) return cudaSuccess;
+    dim3 g((unsigned)((ncols + 255) / 256 < 64 ? (ncols + 255) / 256 : 64), (unsigned)nrows);
+    if (nrows > 65535) return cudaErrorInvalidValue;
+    k_gather_rows<<<g, 256, 0, st>>>(dst, ldd, src, lds, idx, nrows, ncols);
+    return cudaGetLastError();
+}
+
+// B[i][j] = (diag && i == j) ? 1 : 0 on an m x n block
+__global__ void k_fill(uint32_t *__restrict__ B, int64_t ldb, int64_t m, int64_t n, int diag)
+{
+    const int64_t total = m * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx - i * n;
+        B[i * ldb + j] = (diag && i == j) ? 1u : 0u;
+    }
+}
+
+cudaError_t launch_fill(uint32_t *B, int64_t ldb, int64_t m, int64_t n, int diag, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m * n + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_fill<<<(unsigned)nb, 256, 0, st>>>(B, ldb, m, n, diag);
+    return cudaGetLastError();
+}
+
+// flag <- 1 if any entry of the m x n block is nonzero
+__global__ void k_any_nonzero(const uint32_t *__restrict__ B, int64_t ldb, int64_t m, int64_t n, int *flag)
+{
+    const int64_t total = m * n;
+    int any = 0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx - i * n;
+        any |= (B[i * ldb + j] != 0u);
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+cudaError_t launch_any_nonzero(const uint32_t *B, int64_t ldb, int64_t m, int64_t n, int *flag, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m * n + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    k_any_nonzero<<<(unsigned)nb, 256, 0, st>>>(B, ldb, m, n, flag);
+    return cudaGetLastError();
+}
+
+// Copy an m x n block (non-overlapping).
+__global__ void k_copy(uint32_t *__restrict__ D, int64_t ldd, const uint32_t *__restrict__ S, int64_t lds,
+                       int64_t m, int64_t n)
+{
+    const int64_t total = m * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx - i * n;
+        D[i * ldd + j] = S[i * lds + j];
+    }
+}
+
+cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
+                        cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m * n + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_copy<<<(unsigned)nb, 256, 0, st>>>(D, ldd, S, lds, m, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// TRTRI leaf (Algorithm 3 at its base): in-place inverse of an n x n (n <= 64)
+// triangular block, one thread per column j solving T x = e_j.
+// ---------------------------------------------------------------------------
+template <bool UPPER, bool UNIT, bool MONT>
+__global__ void __launch_bounds__(TRI_MAX)
+k_trtri_leaf(uint32_t *__restrict__ T, int64_t ldt, int n, ModP M)
+{
+    __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
+    __shared__ uint32_t sD[TRI_MAX];
+    __shared__ uint32_t sX[TRI_MAX][TRI_MAX + 1];
+    load_tri<UPPER, UNIT, true, MONT>(T, ldt, n, M, sT, sD);
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < n) {
+        if (UPPER) {
+            sX[j][j] = MONT ? redc((uint64_t)sD[j], M) : sD[j];       // plain 1 / U[j][j]
+            for (int i = j - 1; i >= 0; --i) {
+                uint32_t acc = 0u;
+                for (int k = i + 1; k <= j; ++k) acc = addm(acc, mmul<MONT>(sX[k][j], sT[i][k], M), M);
+                const uint32_t v = mmul<MONT>(acc, sD[i], M);
+                sX[i][j] = v ? M.p - v : 0u;
+            }
+        } else {
+            sX[j][j] = MONT ? redc((uint64_t)sD[j], M) : sD[j];
+            for (int i = j + 1; i < n; ++i) {
+                uint32_t acc = 0u;
+                for (int k = j; k < i; ++k) acc = addm(acc, mmul<MONT>(sX[k][j], sT[i][k], M), M);
+                const uint32_t v = mmul<MONT>(acc, sD[i], M);
+                sX[i][j] = v ? M.p - v : 0u;
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, c = idx - i * n;
+        const bool strict = UPPER ? (c > i) : (c < i);
+        if (strict || (!UNIT && c == i)) T[i * ldt + c] = sX[i][c];
+    }
+}
+
+cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int n, ModP M, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n > TRI_MAX) return cudaErrorInvalidValue;
+    const bool mont = (M.p & 1u) != 0;
+#define TRTRI_CASE(U, D)                                                                     \
+    if (mont) k_trtri_leaf<U, D, true><<<1, TRI_MAX, 0, st>>>(T, ldt, n, M);                 \
+    else k_trtri_leaf<U, D, false><<<1, TRI_MAX, 0, st>>>(T, ldt, n, M);
+    if (upper && unit) { TRTRI_CASE(true, true) }
+    else if (upper) { TRTRI_CASE(true, false) }
+    else if (unit) { TRTRI_CASE(false, true) }
+    else { TRTRI_CASE(false, false) }
+#undef TRTRI_CASE
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// TRULM leaf (Algorithm 4 at its base, the variant with unit upper U stored
+// strictly above the diagonal and non-unit lower L on and below it):
+// A <- U L for an n x n (n <= 64) block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_trulm_leaf(uint32_t *__restrict__ A, int64_t lda, int n, ModP M)
+{
+    __shared__ uint32_t sA[TRI_MAX][TRI_MAX + 1];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, c = idx - i * n;
+        sA[i][c] = A[i * lda + c];
+    }
+    __syncthreads();
+    uint32_t out[(TRI_MAX * TRI_MAX + 255) / 256];
+    int cnt = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        // (U L)[i][j] = L[i][j] [i >= j] + sum_{k > i, k >= j} U[i][k] L[k][j]
+        Acc acc = {0ull, 0u};
+        if (i >= j) acc_add(acc, (uint64_t)sA[i][j]);
+        for (int k = (i + 1 > j ? i + 1 : j); k < n; ++k) acc_add(acc, (uint64_t)sA[i][k] * sA[k][j]);
+        out[cnt++] = acc_red(acc, M);
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        A[i * lda + j] = out[cnt++];
+    }
+}
+
+cudaError_t launch_trulm_leaf(uint32_t *A, int64_t lda, int n, ModP M, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n > TRI_MAX) return cudaErrorInvalidValue;
+    k_trulm_leaf<<<1, 256, 0, st>>>(A, lda, n, M);
+    return cudaGetLastError();
+}
+
+// Zero the strict upper triangle of an n x n block.
+__global__ void k_zero_upper(uint32_t *__restrict__ B, int64_t ldb, int64_t n)
+{
+    const int64_t total = n * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx - i * n;
+        if (j > i) B[i * ldb + j] = 0u;
+    }
+}
+
+cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t st)
+{
+    if (n <= 1) return cudaSuccess;
+    int64_t nb = (n * n + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_zero_upper<<<(unsigned)nb, 256, 0, st>>>(B, ldb, n);
+    return cudaGetLastError();
+}

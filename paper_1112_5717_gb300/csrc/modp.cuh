@@ -12,6 +12,8 @@ struct ModP {
     uint32_t p;
     uint32_t r64;     // 2^64 mod p
     uint64_t mu;      // floor((2^64 - 1) / p)
+    uint32_t pneg;    // -p^{-1} mod 2^32 (odd p): Montgomery reduction with R = 2^32
+    uint32_t r2;      // R^2 mod p
 };
 
 static inline ModP make_modp(uint32_t p)
@@ -20,6 +22,12 @@ static inline ModP make_modp(uint32_t p)
     M.p = p;
     M.mu = ~0ull / p;
     M.r64 = (uint32_t)((~0ull % p + 1) % p);
+    // Newton iteration for p^{-1} mod 2^32 (p odd): x <- x (2 - p x) doubles the correct bits
+    uint32_t x = p;
+    for (int i = 0; i < 5; ++i) x *= 2u - p * x;
+    M.pneg = (p & 1u) ? (uint32_t)(0u - x) : 0u;
+    uint64_t r = (1ull << 32) % p;
+    M.r2 = (uint32_t)(r * r % p);
     return M;
 }
 
@@ -54,6 +62,35 @@ __device__ __forceinline__ uint32_t ffupd(uint32_t f, uint32_t x, uint32_t m, ui
 {
     uint32_t nm = m ? M.p - m : 0u;
     return red64((uint64_t)f * x + (uint64_t)nm * y, M);
+}
+
+// Montgomery reduction (odd p, R = 2^32): for T < p R returns T R^{-1} mod p.
+// T + m p < 2 p R <= 2^64 for p < 2^31, and the result before the final
+// subtraction is below 2p.
+__device__ __forceinline__ uint32_t redc(uint64_t T, const ModP &M)
+{
+    const uint32_t m = (uint32_t)T * M.pneg;
+    const uint32_t t = (uint32_t)((T + (uint64_t)m * M.p) >> 32);
+    return t >= M.p ? t - M.p : t;
+}
+
+// R^{-1} (f x - m y) mod p with one reduction: f x + (p - m) y < 2 p^2 < p R.
+__device__ __forceinline__ uint32_t ffupd_mont(uint32_t f, uint32_t x, uint32_t m, uint32_t y, const ModP &M)
+{
+    const uint32_t nm = m ? M.p - m : 0u;
+    return redc((uint64_t)f * x + (uint64_t)nm * y, M);
+}
+
+// a^(p-2) mod p with Montgomery products (odd p): the inverse of a nonzero residue.
+__device__ __forceinline__ uint32_t invm_mont(uint32_t a, const ModP &M)
+{
+    uint32_t b = redc((uint64_t)a * M.r2, M);            // a R
+    uint32_t r = redc((uint64_t)M.r2, M);                // R (one in Montgomery form)
+    for (uint32_t e = M.p - 2; e; e >>= 1) {
+        if (e & 1u) r = redc((uint64_t)r * b, M);
+        b = redc((uint64_t)b * b, M);
+    }
+    return redc((uint64_t)r, M);                         // back from Montgomery form
 }
 
 // a^(p-2) mod p (Fermat), the inverse of a nonzero residue.
