@@ -44,7 +44,8 @@ typedef enum {
     CUP_ERR_CUDA = -4,         /* a CUDA call failed (see cup_last_cuda_error) */
     CUP_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired */
     CUP_ERR_NOMEM = -6,        /* workspace allocation failed */
-    CUP_ERR_UNSUPPORTED = -7   /* valid request this build cannot serve */
+    CUP_ERR_UNSUPPORTED = -7,  /* valid request this build cannot serve */
+    CUP_ERR_TOO_LARGE = -8     /* cup_mm_sub_noalloc: the product needs more scratch than it has */
 } cup_status;
 
 typedef struct cup_handle cup_handle;
@@ -220,6 +221,31 @@ cup_status cup_trtri(cup_handle *handle, int flags, uint32_t *T, int64_t ldt, in
  * strictly above the diagonal and L lower triangular stored on and below it;
  * A <- U L in place. */
 cup_status cup_trulm(cup_handle *handle, uint32_t *A, int64_t lda, int64_t n, uint32_t p, void *stream);
+
+/* Allocation-free Schur update: C <- C - A B mod p on the tensor engine,
+ * like cup_mm_sub with CUP_ENGINE_TENSOR, for callers that must not allocate
+ * device memory (for example code that runs while a stream is being captured
+ * into a CUDA graph, a process whose device memory is owned by its own
+ * fixed-size pool, or a latency-bound loop where an allocation is not
+ * acceptable). The paper has no counterpart: this is a packaging choice.
+ *   - No handle and no allocation: the 8-bit limb planes live in one fixed
+ *     scratch array of 16 MiB that the library holds on every GPU where it
+ *     is loaded, until the process exits. A product needs
+ *     L * (M + N) * roundup(K, 64) * 2 bytes of it (L = 1, 2, 3, 4 limbs for
+ *     p below 2^8, 2^16, 2^24, 2^31); larger products return
+ *     CUP_ERR_TOO_LARGE without touching C.
+ *   - Runs on the current CUDA device. The first call on a device looks up
+ *     the scratch array's device address (and sets the kernel's shared-memory
+ *     limit); make that first call before any stream capture.
+ *   - Every call on a device shares the one scratch array and its error word:
+ *     calls that can overlap on the GPU (different streams, or several host
+ *     threads) race and must be serialised by the caller. Each call rewrites
+ *     the part of the scratch it reads and clears the error word first.
+ *   - Synchronises `stream` before returning; CUP_ERR_TIMEOUT if a bounded
+ *     device-side wait expired. Arguments as for cup_mm_sub. */
+cup_status cup_mm_sub_noalloc(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                              const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                              uint32_t p, void *stream);
 
 /* Column transpositions (Sec. 1.1): for t = k0..k1-1 in order, swap columns t
  * and d_ipiv[t] of rows row0..row0+nrows-1 of A (A <- A P^T restricted to

@@ -37,7 +37,7 @@ class Stats(ctypes.Structure):
 
 STATUS = {0: "CUP_OK", 1: "CUP_SINGULAR", 2: "CUP_INCONSISTENT", -1: "CUP_ERR_ARG",
           -2: "CUP_ERR_PRIME", -3: "CUP_ERR_VALUE", -4: "CUP_ERR_CUDA", -5: "CUP_ERR_TIMEOUT",
-          -6: "CUP_ERR_NOMEM", -7: "CUP_ERR_UNSUPPORTED"}
+          -6: "CUP_ERR_NOMEM", -7: "CUP_ERR_UNSUPPORTED", -8: "CUP_ERR_TOO_LARGE"}
 
 # Every entry point of include/cup_gb300.h with its ctypes signature.
 _P = ctypes.c_void_p
@@ -67,6 +67,7 @@ SIGNATURES = {
     "cup_trmm": (_INT, [_P, _INT, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
     "cup_trtri": (_INT, [_P, _INT, _P, _I64, _I64, _U32, _P]),
     "cup_trulm": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
+    "cup_mm_sub_noalloc": (_INT, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _P]),
 }
 
 LEFT, UPPER, UNIT = 1, 2, 4

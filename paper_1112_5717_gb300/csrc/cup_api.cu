@@ -481,6 +481,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+bool cup_internal_prime_ok(uint32_t p) { return check_prime(p) == CUP_OK; }
+
 extern "C" {
 
 cup_status cup_create(cup_handle **handle, int device)

@@ -74,3 +74,6 @@ cudaError_t launch_any_nonzero(const uint32_t *B, int64_t ldb, int64_t m, int64_
 cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
                         cudaStream_t st);
 cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t st);
+
+// Prime check shared by the entry points (cup_api.cu).
+bool cup_internal_prime_ok(uint32_t p);

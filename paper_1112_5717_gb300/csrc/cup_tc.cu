@@ -19,7 +19,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <mutex>
 #include "cup_internal.cuh"
+#include "../../include/cup_gb300.h"
 
 namespace tc {
 
@@ -493,4 +495,57 @@ cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B
     case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
     default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free Schur update (cup_mm_sub_noalloc): the limb planes live in a
+// fixed scratch array of the module instead of handle-owned memory.
+// ---------------------------------------------------------------------------
+#define CUP_NOALLOC_SCRATCH_BYTES (16u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CUP_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) int g_noalloc_err[64];
+
+namespace {
+struct NoallocDev {
+    bool ready = false;
+    void *scratch = nullptr;
+    int *err = nullptr;
+};
+constexpr int kNoallocDevs = 64;
+NoallocDev g_noalloc_dev[kNoallocDevs];
+std::mutex g_noalloc_mu;
+}  // namespace
+
+extern "C" cup_status cup_mm_sub_noalloc(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                                         const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                                         uint32_t p, void *stream)
+{
+    if (M < 0 || N < 0 || K < 0) return CUP_ERR_ARG;
+    if (!cup_internal_prime_ok(p)) return CUP_ERR_PRIME;
+    if (M == 0 || N == 0 || K == 0) return CUP_OK;
+    if (!C || !A || !B || ldc < N || lda < K || ldb < N) return CUP_ERR_ARG;
+    if (tc_workspace_bytes(p, M, N, K) > (size_t)CUP_NOALLOC_SCRATCH_BYTES) return CUP_ERR_TOO_LARGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocDevs) return CUP_ERR_CUDA;
+    NoallocDev &d = g_noalloc_dev[dev];
+    {
+        // once per device, with that device current: device addresses of the scratch
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!d.ready) {
+            void *ws = nullptr, *err = nullptr;
+            if (cudaGetSymbolAddress(&ws, g_noalloc_scratch) != cudaSuccess) return CUP_ERR_CUDA;
+            if (cudaGetSymbolAddress(&err, g_noalloc_err) != cudaSuccess) return CUP_ERR_CUDA;
+            d.scratch = ws;
+            d.err = (int *)err;
+            d.ready = true;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d.err, 0, sizeof(int), st) != cudaSuccess) return CUP_ERR_CUDA;
+    if (launch_gemm_sub_tc(A, lda, B, ldb, C, ldc, M, N, K, make_modp(p), d.scratch, d.err, st) != cudaSuccess)
+        return CUP_ERR_CUDA;
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, d.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CUP_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CUP_ERR_CUDA;
+    return herr ? CUP_ERR_TIMEOUT : CUP_OK;
 }
