@@ -224,7 +224,9 @@ def run_ours(args):
     opts = {k: v for k, v in (("leaf_rows", args.leaf_rows), ("window", args.window),
                               ("tc_min_k", args.tc_min_k)) if v is not None}
     h = cup.Handle(dev, engine=engine, profile=args.profile, **opts)
-    stream = torch.cuda.current_stream()
+    # a stream of our own: calls repeated on it are replayed as one CUDA graph
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     def one_step():
         A.copy_(A0)

@@ -64,7 +64,10 @@ enum {
     CUP_OPT_WINDOW = 2,        /* pivot-search window of the base case, 1..128 (default 96) */
     CUP_OPT_TC_MIN_K = 3,      /* smallest inner dimension sent to the tensor engine (default 64) */
     CUP_OPT_VALIDATE = 4,      /* nonzero: check inputs are canonical residues (slow) */
-    CUP_OPT_PROFILE = 5        /* 1: time every Schur-update launch with CUDA events; 2: every launch */
+    CUP_OPT_PROFILE = 5,       /* 1: time every Schur-update launch with CUDA events; 2: every launch */
+    CUP_OPT_SCHEDULE = 6       /* cup_factor schedule: 1 (default) device-resident, replayed as a CUDA
+                                  graph when a call repeats; 2 device-resident without graphs; 0 host-driven
+                                  (reads each block's rank back before launching the next) */
 };
 
 /* Counters of the work a handle has enqueued since the last cup_reset_stats.
@@ -176,6 +179,32 @@ cup_status cup_class_ms(cup_handle *handle, double *out8);
 
 /* Zero the counters of a handle. */
 cup_status cup_reset_stats(cup_handle *handle);
+
+/* One matrix of a batched call (all pointers are DEVICE pointers). */
+typedef struct {
+    uint32_t *A;           /* m x n row-major (lda), residues in [0, p); receives [C\U] */
+    int64_t m, n, lda;
+    uint32_t p;            /* this matrix's prime, below 2^31 */
+    uint32_t reserved;
+    int64_t *profile;      /* min(m, n) entries: row rank profile (first rank valid) */
+    int64_t *ipiv;         /* min(m, n) entries: column transpositions as in cup_factor */
+} cup_batch_item;
+
+/*
+ * Batched CUP (Algorithm 6's output for each matrix, as cup_factor) of
+ * `count` independent matrices, each over its own prime field, in one
+ * persistent launch; nothing is read back to the host, so the call is
+ * asynchronous and can be captured in a CUDA graph. Matrices with
+ * min(m, n) <= 2048 are supported.
+ *   d_items  device array of `count` items.
+ *   d_rank   device int64[count]: the rank of each matrix, or -1 if its item
+ *            was invalid (bad sizes or pointers, p not a prime below 2^31,
+ *            min(m, n) > 2048).
+ *   d_det    device uint32[count] or NULL: det(A) mod p for square matrices
+ *            (0 when singular or not square).
+ */
+cup_status cup_factor_batched(cup_handle *handle, const cup_batch_item *d_items, int64_t count,
+                              int64_t *d_rank, uint32_t *d_det, void *stream);
 
 /* ---- Building blocks of the hot path (exposed for testing and reuse) ---- */
 

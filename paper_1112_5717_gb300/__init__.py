@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libcup_gb300.so")
 
 ENGINE_PLAIN = 0
 ENGINE_TENSOR = 1
-OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE, OPT_PROFILE = 0, 1, 2, 3, 4, 5
+OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE, OPT_PROFILE, OPT_SCHEDULE = 0, 1, 2, 3, 4, 5, 6
 
 
 class Stats(ctypes.Structure):
@@ -68,7 +68,15 @@ SIGNATURES = {
     "cup_trtri": (_INT, [_P, _INT, _P, _I64, _I64, _U32, _P]),
     "cup_trulm": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
     "cup_mm_sub_noalloc": (_INT, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _P]),
+    "cup_factor_batched": (_INT, [_P, _P, _I64, _P, _P, _P]),
 }
+
+
+class BatchItem(ctypes.Structure):
+    """Mirror of cup_batch_item (include/cup_gb300.h)."""
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("p", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("profile", ctypes.c_void_p), ("ipiv", ctypes.c_void_p)]
 
 LEFT, UPPER, UNIT = 1, 2, 4
 
@@ -136,7 +144,7 @@ class Handle:
         if engine is not None:
             self.set_option(OPT_ENGINE, engine)
         names = {"leaf_rows": OPT_LEAF_ROWS, "window": OPT_WINDOW, "tc_min_k": OPT_TC_MIN_K,
-                 "validate": OPT_VALIDATE, "profile": OPT_PROFILE}
+                 "validate": OPT_VALIDATE, "profile": OPT_PROFILE, "schedule": OPT_SCHEDULE}
         for k, v in opts.items():
             self.set_option(names[k], int(v))
 
@@ -158,7 +166,8 @@ class Handle:
     def class_ms(self) -> dict:
         arr = (ctypes.c_double * 8)()
         self._check(self.lib.cup_class_ms(self.h, arr), "cup_class_ms", self.h)
-        names = ["tc_gemm", "cc_gemm", "slab_pivots", "slab_finish", "trsm_leaf", "laswp", "r6", "r7"]
+        names = ["tc_gemm", "cc_gemm", "slab_pivots", "slab_finish", "trsm_leaf", "laswp", "tc_gemm_with_split",
+                 "untimed"]
         return {k: arr[i] for i, k in enumerate(names)}
 
     def reset_stats(self):
@@ -303,6 +312,36 @@ class Handle:
             raise ValueError("square matrix needed")
         st = self.lib.cup_trulm(self.h, A.data_ptr(), lda, n, p, _stream_ptr(stream))
         self._check(st, "cup_trulm", self.h)
+
+    def factor_batched(self, mats, primes, want_det: bool = False, stream=None):
+        """Batched in-place CUP: mats is a list of int32 CUDA matrices, primes a list of
+        primes. Returns (ranks, profiles, ipivs, dets) as device tensors; profile and
+        ipiv of matrix b are views of length min(m, n). One launch, no host sync."""
+        torch = _torch()
+        count = len(mats)
+        dev = mats[0].device if count else torch.device("cuda")
+        ks = [max(min(t.shape[0], t.shape[1]), 1) for t in mats]
+        offs = [0]
+        for k in ks:
+            offs.append(offs[-1] + k)
+        prof = torch.empty(max(offs[-1], 1), dtype=torch.int64, device=dev)
+        ipiv = torch.empty(max(offs[-1], 1), dtype=torch.int64, device=dev)
+        items = (BatchItem * max(count, 1))()
+        for b, (t, p) in enumerate(zip(mats, primes)):
+            m, n, lda = _mat(t, "A")
+            items[b] = BatchItem(t.data_ptr(), m, n, lda, int(p), 0,
+                                 prof.data_ptr() + 8 * offs[b], ipiv.data_ptr() + 8 * offs[b])
+        raw = torch.frombuffer(bytearray(items), dtype=torch.uint8)
+        d_items = raw.to(dev)
+        ranks = torch.empty(max(count, 1), dtype=torch.int64, device=dev)
+        dets = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if want_det else None
+        st = self.lib.cup_factor_batched(self.h, d_items.data_ptr(), count, ranks.data_ptr(),
+                                         dets.data_ptr() if want_det else None, _stream_ptr(stream))
+        self._check(st, "cup_factor_batched", self.h)
+        self._keep = d_items                     # alive until the stream has used it
+        profs = [prof[offs[b]:offs[b] + ks[b]] for b in range(count)]
+        ipivs = [ipiv[offs[b]:offs[b] + ks[b]] for b in range(count)]
+        return ranks[:count], profs, ipivs, (dets[:count] if want_det else None)
 
     def laswp_cols(self, A, ipiv, k0: int, k1: int, row0: int = 0, nrows: int | None = None,
                    stream=None):

@@ -36,11 +36,32 @@ struct cup_handle {
     int *d_count = nullptr;
     int *h_pinned = nullptr;
     int *d_err = nullptr;          // device-side error word of the tensor-core kernels
+    unsigned long long *d_next = nullptr;   // work counter of the batched kernel
     void *d_ws = nullptr;          // limb planes of the tensor-core Schur update
     size_t ws_bytes = 0;
     int profile = 0;
+    int schedule = 1;              // 0: host-driven recursion, 1: device-resident (+ graph replay)
+    int use_graph = 1;
+    int64_t *d_rank_at = nullptr;  // device-resident schedule: rank before each leaf
+    int64_t rank_at_cap = 0;
+    uint32_t *d_backup = nullptr;  // input copy for the exact fallback
+    size_t backup_bytes = 0;
+    int64_t *h_rank = nullptr;     // pinned copy of rank_at after a device-resident run
+    int64_t h_rank_cap = 0;
+    struct Timed;
+    struct GraphEntry {
+        uint32_t *A; int64_t m, n, lda; uint32_t p; int64_t *prof, *ipiv; cudaStream_t st;
+        int leaf_rows, window, engine; int64_t tc_min_k; int64_t gen; cudaGraphExec_t exec;
+        int64_t launches;                 // kernels per replay
+        bool no_capture;                  // capture failed once: stay eager
+        std::vector<int> timed;           // indices into graph_timed, read after each replay
+        std::vector<GemmDesc> gemms;      // the Schur updates it runs (extents resolved per replay)
+    };
+    int64_t gen = 0;                   // bumped whenever a buffer a graph may reference moves
+    std::vector<GraphEntry> graphs;
     cup_stats stats = {};
     struct Timed { cudaEvent_t e0, e1; double limb_flops, field_flops; int cls; };
+    std::vector<Timed> graph_timed;    // event pairs baked into captured graphs
     double cls_ms[8] = {0};        // per kernel class, profile level >= 2
     std::vector<Timed> pending;    // recorded intervals not yet read
     std::vector<cudaEvent_t> evpool;
@@ -178,6 +199,7 @@ cup_status ensure_pairs(cup_handle *h, int64_t need)
     h->pairs_cap = 0;
     CU(cudaMalloc(&h->d_pairs, (size_t)need * sizeof(int2)));
     h->pairs_cap = need;
+    ++h->gen;
     return CUP_OK;
 }
 
@@ -201,6 +223,7 @@ cup_status ensure_ws(cup_handle *h, size_t bytes)
     h->ws_bytes = 0;
     CU(cudaMalloc(&h->d_ws, bytes));
     h->ws_bytes = bytes;
+    ++h->gen;
     return CUP_OK;
 }
 
@@ -224,8 +247,8 @@ cup_status laswp(Ctx &c, int64_t row0, int64_t nrows, int64_t k0, int64_t k1)
     if (nrows <= 0 || k1 <= k0) return CUP_OK;
     CK(ensure_pairs(h, k1 - k0));
     ClassTimer tm(h, c.st, 5);
-    CU(launch_swaplist(c.ipiv, k0, k1, h->d_pairs, h->d_count, c.st));
-    CU(launch_laswp(c.A, c.lda, row0, nrows, h->d_pairs, h->d_count, c.st));
+    CU(launch_swaplist(c.ipiv, dconst(k0), dconst(k1), h->d_pairs, h->d_count, c.st));
+    CU(launch_laswp(c.A, c.lda, dconst(row0), dconst(nrows), h->d_pairs, h->d_count, c.st));
     h->stats.launches += 2;
     return CUP_OK;
 }
@@ -428,13 +451,13 @@ cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_ou
     if (mrows <= h->leaf_rows) {
         {
         ClassTimer tm(h, c.st, 2);
-        CU(launch_slab_pivots(c.A, c.lda, a, (int)mrows, col0, w, h->window, 0, c.M, h->d_slab,
-                              c.ipiv, c.prof, c.st));
+        CU(launch_slab_pivots(c.A, c.lda, a, (int)mrows, dconst(col0), c.n, h->window, 0, c.M, h->d_slab,
+                              c.ipiv, c.prof, nullptr, c.st));
         }
         CU(cudaMemcpyAsync(h->h_pinned, h->d_slab, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
         {
         ClassTimer tm(h, c.st, 3);
-        CU(launch_slab_finish(c.A, c.lda, a, col0, w, c.M, h->d_slab, c.st));
+        CU(launch_slab_finish(c.A, c.lda, a, dconst(col0), c.n, c.M, h->d_slab, nullptr, c.st));
         }
         h->stats.launches += 2;
         CK(sync_stream(h, c.st));
@@ -465,6 +488,154 @@ cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_ou
     return CUP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Device-resident schedule of Algorithm 6. The recursion tree over rows is
+// fixed by m and the leaf size; what depends on the data (the rank of the
+// rows above a block, col0, and of its top half, mid) is read by every kernel
+// from rank_at[], which the base-case kernels fill in as they run. Nothing is
+// read back until the end, so the whole factorisation is one stream of
+// launches (and one CUDA graph when replayed). Rows whose pivot-window
+// residual vanishes are taken as dependent and checked by the finish kernel;
+// if a check fails the call is redone host-driven from a copy of the input.
+// ---------------------------------------------------------------------------
+struct DevCtx {
+    cup_handle *h;
+    uint32_t *A;
+    int64_t lda, m, n;
+    ModP M;
+    int64_t *ipiv, *prof, *rank_at;
+    cudaStream_t st;
+    int nleaf;
+    std::vector<GemmDesc> *gemms;     // every Schur update enqueued (extents resolved after the run)
+};
+
+// Host evaluation of a Dyn whose pointers point into the device array dbase,
+// given a host copy hbase of that array.
+int64_t host_eval(const Dyn &d, const int64_t *dbase, const int64_t *hbase)
+{
+    int64_t v = d.s;
+    if (d.p0) v += d.c0 * hbase[d.p0 - dbase];
+    if (d.p1) v += d.c1 * hbase[d.p1 - dbase];
+    return v < d.lo ? d.lo : (v > d.hi ? d.hi : v);
+}
+
+cup_status dev_gemm(DevCtx &c, const GemmDesc &g)
+{
+    cup_handle *h = c.h;
+    if (g.M <= 0 || g.N.hi <= 0 || g.K.hi <= 0) return CUP_OK;
+    const bool tc = h->engine == CUP_ENGINE_TENSOR && g.K.hi >= h->tc_min_k;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profile) { e0 = take_event(h); e1 = take_event(h); }
+    if (tc) {
+        ClassTimer tm(h, c.st, 6);
+        CU(launch_gemm_tc_desc(g, c.M, h->d_ws, h->d_err, c.st, e0, e1));
+        h->stats.launches += 3;
+    } else {
+        if (e0) cudaEventRecord(e0, c.st);
+        CU(launch_gemm_cc_desc(g, c.M, c.st));
+        if (e1) cudaEventRecord(e1, c.st);
+        h->stats.launches += 1;
+    }
+    if (h->profile) h->pending.push_back({e0, e1, 0.0, 0.0, tc ? 0 : 1});
+    GemmDesc rec = g;
+    rec.add = tc ? 1 : 0;               // reused as the engine tag in the record
+    c.gemms->push_back(rec);
+    return CUP_OK;
+}
+
+cup_status dev_laswp(DevCtx &c, Dyn row0, Dyn nrows, Dyn k0, Dyn k1)
+{
+    cup_handle *h = c.h;
+    if (nrows.hi <= 0 || k1.hi <= k0.lo) return CUP_OK;
+    ClassTimer tm(h, c.st, 5);
+    CU(launch_swaplist(c.ipiv, k0, k1, h->d_pairs, h->d_count, c.st));
+    CU(launch_laswp(c.A, c.lda, row0, nrows, h->d_pairs, h->d_count, c.st));
+    h->stats.launches += 2;
+    return CUP_OK;
+}
+
+// TRSM(Right, Upper, Unit) on columns [j0, j0 + len) of the block [col0, mid):
+// Algorithm 2 with the split fixed by the static bound len and every extent
+// clamped to r1 = mid - col0 on the device.
+cup_status dev_trsm(DevCtx &c, const int64_t *col0p, const int64_t *midp, int64_t a2, int64_t m2, int64_t j0,
+                    int64_t len)
+{
+    cup_handle *h = c.h;
+    if (len <= 0) return CUP_OK;
+    if (len <= 64) {
+        TriDesc d{c.A, c.lda, dvar(j0, col0p, 1, nullptr, 0, 0, c.n), dvar(j0, col0p, 1, nullptr, 0, 0, c.n),
+                  c.A, c.lda, dconst(a2), dvar(j0, col0p, 1, nullptr, 0, 0, c.n), m2,
+                  dvar(-j0, midp, 1, col0p, -1, 0, len)};
+        ClassTimer tm(h, c.st, 4);
+        CU(launch_trsm_ruu_desc(d, c.M, c.st));
+        h->stats.launches += 1;
+        return CUP_OK;
+    }
+    const int64_t k = ((len / 2) + 63) / 64 * 64;
+    CK(dev_trsm(c, col0p, midp, a2, m2, j0, k));
+    GemmDesc g{c.A, c.lda, dconst(a2), dvar(j0, col0p, 1, nullptr, 0, 0, c.n),
+               c.A, c.lda, dvar(j0, col0p, 1, nullptr, 0, 0, c.n), dvar(j0 + k, col0p, 1, nullptr, 0, 0, c.n),
+               c.A, c.lda, dconst(a2), dvar(j0 + k, col0p, 1, nullptr, 0, 0, c.n),
+               m2, dvar(-j0 - k, midp, 1, col0p, -1, 0, len - k), dvar(-j0, midp, 1, col0p, -1, 0, k), 0};
+    CK(dev_gemm(c, g));
+    CK(dev_trsm(c, col0p, midp, a2, m2, j0 + k, len - k));
+    return CUP_OK;
+}
+
+cup_status dev_rec(DevCtx &c, int64_t a, int64_t mrows)
+{
+    cup_handle *h = c.h;
+    if (mrows <= 0) return CUP_OK;
+    if (mrows <= h->leaf_rows) {
+        const int L = c.nleaf++;
+        const Dyn col0 = dvar(0, c.rank_at + L, 1, nullptr, 0, 0, c.n);
+        {
+            ClassTimer tm(h, c.st, 2);
+            CU(launch_slab_pivots(c.A, c.lda, a, (int)mrows, col0, c.n, h->window, 1, c.M, h->d_slab, c.ipiv,
+                                  c.prof, c.rank_at + L + 1, c.st));
+        }
+        {
+            ClassTimer tm(h, c.st, 3);
+            CU(launch_slab_finish(c.A, c.lda, a, col0, c.n, c.M, h->d_slab, h->d_err, c.st));
+        }
+        h->stats.launches += 2;
+        return CUP_OK;
+    }
+    const int64_t nl = (mrows + h->leaf_rows - 1) / h->leaf_rows;
+    const int64_t k = ((nl + 1) / 2) * h->leaf_rows;
+    const int L0 = c.nleaf;
+    CK(dev_rec(c, a, k));
+    const int Lm = c.nleaf;
+    const int64_t *col0p = c.rank_at + L0, *midp = c.rank_at + Lm;
+    const int64_t a2 = a + k, m2 = mrows - k, kmax = k < c.n ? k : c.n;
+    // A2 <- A2 P1^T
+    CK(dev_laswp(c, dconst(a2), dconst(m2), dvar(0, col0p, 1, nullptr, 0, 0, c.n), dvar(0, midp, 1, nullptr, 0, 0, c.n)));
+    // G <- A21 U1^{-1}
+    CK(dev_trsm(c, col0p, midp, a2, m2, 0, kmax));
+    // H <- A22 - G V1
+    GemmDesc g{c.A, c.lda, dconst(a2), dvar(0, col0p, 1, nullptr, 0, 0, c.n),
+               c.A, c.lda, dvar(0, col0p, 1, nullptr, 0, 0, c.n), dvar(0, midp, 1, nullptr, 0, 0, c.n),
+               c.A, c.lda, dconst(a2), dvar(0, midp, 1, nullptr, 0, 0, c.n),
+               m2, dvar(c.n, midp, -1, nullptr, 0, 0, c.n), dvar(0, midp, 1, col0p, -1, 0, kmax), 0};
+    CK(dev_gemm(c, g));
+    CK(dev_rec(c, a2, m2));
+    const int L1 = c.nleaf;
+    const int64_t *endp = c.rank_at + L1;
+    // V1 <- V1 P2^T
+    CK(dev_laswp(c, dvar(0, col0p, 1, nullptr, 0, 0, c.n), dvar(0, midp, 1, col0p, -1, 0, kmax),
+                 dvar(0, midp, 1, nullptr, 0, 0, c.n), dvar(0, endp, 1, nullptr, 0, 0, c.n)));
+    return CUP_OK;
+}
+
+int64_t count_leaves(int64_t mrows, int leaf_rows)
+{
+    if (mrows <= 0) return 0;
+    if (mrows <= leaf_rows) return 1;
+    const int64_t nl = (mrows + leaf_rows - 1) / leaf_rows;
+    const int64_t k = ((nl + 1) / 2) * leaf_rows;
+    return count_leaves(k, leaf_rows) + count_leaves(mrows - k, leaf_rows);
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -482,6 +653,185 @@ struct DeviceGuard {
 }  // namespace
 
 bool cup_internal_prime_ok(uint32_t p) { return check_prime(p) == CUP_OK; }
+
+cudaError_t launch_cup_batched(const cup_batch_item *items, int64_t count, int64_t *ranks, uint32_t *dets,
+                               unsigned long long *next, int grid, cudaStream_t st);
+
+#define CUP_ERR_SPECULATION_INTERNAL ((cup_status)-100)
+
+namespace {
+
+cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                         int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, cudaStream_t st)
+{
+    const int64_t nleaves = count_leaves(m, h->leaf_rows);
+    if (nleaves + 1 > h->rank_at_cap) {
+        if (h->d_rank_at) cudaFree(h->d_rank_at);
+        h->d_rank_at = nullptr;
+        h->rank_at_cap = 0;
+        CU(cudaMalloc(&h->d_rank_at, (size_t)(nleaves + 1) * sizeof(int64_t)));
+        h->rank_at_cap = nleaves + 1;
+        ++h->gen;
+    }
+    const size_t bbytes = (size_t)m * (size_t)n * 4;
+    if (bbytes > h->backup_bytes) {
+        if (h->d_backup) cudaFree(h->d_backup);
+        h->d_backup = nullptr;
+        h->backup_bytes = 0;
+        CU(cudaMalloc(&h->d_backup, bbytes));
+        h->backup_bytes = bbytes;
+        ++h->gen;
+    }
+    CK(ensure_pairs(h, n));
+    if (h->engine == CUP_ENGINE_TENSOR) {
+        // the largest product: rows below the first split, all columns, inner size up to that split
+        const int64_t nl = (m + h->leaf_rows - 1) / h->leaf_rows;
+        const int64_t ktop = m > h->leaf_rows ? ((nl + 1) / 2) * h->leaf_rows : 0;
+        if (ktop > 0) CK(ensure_ws(h, tc_workspace_bytes(p, m, n, ktop < n ? ktop : n)));
+    }
+    if (nleaves + 1 > h->h_rank_cap) {
+        if (h->h_rank) cudaFreeHost(h->h_rank);
+        h->h_rank = nullptr;
+        h->h_rank_cap = 0;
+        CU(cudaMallocHost(&h->h_rank, (size_t)(nleaves + 1) * sizeof(int64_t)));
+        h->h_rank_cap = nleaves + 1;
+        ++h->gen;
+    }
+    const ModP M = make_modp(p);
+    // graph replay for a repeated call with the same buffers and options
+    cup_handle::GraphEntry *ge = nullptr;
+    for (auto &e : h->graphs)
+        if (e.A == A && e.m == m && e.n == n && e.lda == lda && e.p == p && e.prof == d_profile &&
+            e.ipiv == d_ipiv && e.st == st && e.leaf_rows == h->leaf_rows && e.window == h->window &&
+            e.engine == h->engine && e.tc_min_k == h->tc_min_k)
+            ge = &e;
+    if (ge && ge->gen != h->gen) {
+        if (ge->exec) cudaGraphExecDestroy(ge->exec);
+        ge->exec = nullptr;
+        ge->gen = h->gen;
+    }
+    auto enqueue = [&](std::vector<GemmDesc> &gl) -> cup_status {
+        CU(cudaMemcpy2DAsync(h->d_backup, (size_t)n * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m,
+                             cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemsetAsync(h->d_rank_at, 0, sizeof(int64_t), st));
+        CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+        DevCtx c{h, A, lda, m, n, M, d_ipiv, d_profile, h->d_rank_at, st, 0, &gl};
+        CK(dev_rec(c, 0, m));
+        CU(cudaMemcpyAsync(h->h_rank, h->d_rank_at, (size_t)(nleaves + 1) * sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(h->h_pinned + 8, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        return CUP_OK;
+    };
+    const int64_t launches0 = h->stats.launches;
+    // the legacy default stream cannot be captured
+    const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread && h->profile == 0;
+    std::vector<GemmDesc> gl_local;
+    const std::vector<GemmDesc> *glist = &gl_local;
+    const std::vector<int> *timed_now = nullptr;
+    if (ge && ge->exec && capturable) {
+        CU(cudaGraphLaunch(ge->exec, st));
+        h->stats.launches += ge->launches;
+        glist = &ge->gemms;
+        timed_now = &ge->timed;
+    } else if (ge && h->use_graph && capturable && !ge->no_capture) {
+        const size_t pend0 = h->pending.size();
+        ge->gemms.clear();
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cup_status s = CUP_ERR_CUDA;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            s = enqueue(ge->gemms);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (s == CUP_OK && e == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+                exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        if (!exec) {
+            // capture is not available here: run this and later identical calls eagerly
+            cudaGetLastError();
+            ge->no_capture = true;
+            for (size_t i = pend0; i < h->pending.size(); ++i) {
+                if (h->pending[i].e0) h->evpool.push_back(h->pending[i].e0);
+                if (h->pending[i].e1) h->evpool.push_back(h->pending[i].e1);
+            }
+            h->pending.resize(pend0);
+            h->stats.launches = launches0;
+            ge->gemms.clear();
+            return factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st);
+        }
+        ge->exec = exec;
+        ge->launches = h->stats.launches - launches0;
+        // event pairs recorded during capture stay with the graph
+        ge->timed.clear();
+        for (size_t i = pend0; i < h->pending.size(); ++i) {
+            ge->timed.push_back((int)h->graph_timed.size());
+            h->graph_timed.push_back(h->pending[i]);
+        }
+        h->pending.resize(pend0);
+        CU(cudaGraphLaunch(exec, st));
+        glist = &ge->gemms;
+        timed_now = &ge->timed;
+    } else {
+        if (!ge && h->use_graph && capturable) {
+            // remember the call; the next identical one is captured and replayed
+            cup_handle::GraphEntry e{A, m, n, lda, p, d_profile, d_ipiv, st, h->leaf_rows, h->window, h->engine,
+                                     h->tc_min_k, h->gen, nullptr, 0, false, {}, {}};
+            if (h->graphs.size() > 16) {
+                if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
+                h->graphs.erase(h->graphs.begin());
+            }
+            h->graphs.push_back(e);
+        }
+        CK(enqueue(gl_local));
+    }
+    CK(sync_stream(h, st));
+    if (timed_now)
+        for (int ti : *timed_now) {
+            auto &t = h->graph_timed[ti];
+            float ms = 0.f;
+            if (t.e0 && t.e1 && cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+                if (t.cls == 0) h->stats.tc_ms += ms;
+                else if (t.cls == 1) h->stats.cc_ms += ms;
+                h->cls_ms[t.cls] += ms;
+            } else {
+                cudaGetLastError();          // an interval the graph could not time: leave it out
+                h->cls_ms[7] += 1.0;         // count of such intervals
+            }
+        }
+    const int64_t r = h->h_rank[nleaves];
+    const int err = h->h_pinned[8];
+    if (err == 0) {
+        // the extents each Schur update actually had, from the ranks this run produced
+        const int L = tc_limbs(p);
+        for (const auto &g : *glist) {
+            const double f = 2.0 * (double)g.M * (double)host_eval(g.N, h->d_rank_at, h->h_rank) *
+                             (double)host_eval(g.K, h->d_rank_at, h->h_rank);
+            if (g.add) {
+                h->stats.tc_launches += 1;
+                h->stats.tc_field_flops += f;
+                h->stats.tc_limb_flops += f * L * L;
+            } else {
+                h->stats.cc_launches += 1;
+                h->stats.cc_field_flops += f;
+            }
+        }
+    }
+    if (err == CUP_DEVERR_SPECULATION) {
+        CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+        return CUP_ERR_SPECULATION_INTERNAL;
+    }
+    if (err != 0) {
+        snprintf(h->err, sizeof(h->err), "device wait expired (site %d)", err);
+        CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+        return CUP_ERR_TIMEOUT;
+    }
+    *rank = r;
+    return CUP_OK;
+}
+
+}  // namespace
+
+
 
 extern "C" {
 
@@ -509,7 +859,13 @@ cup_status cup_destroy(cup_handle *h)
         if (h->d_count) cudaFree(h->d_count);
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
         if (h->d_err) cudaFree(h->d_err);
+        if (h->d_next) cudaFree(h->d_next);
         if (h->d_ws) cudaFree(h->d_ws);
+        if (h->d_rank_at) cudaFree(h->d_rank_at);
+        if (h->d_backup) cudaFree(h->d_backup);
+        if (h->h_rank) cudaFreeHost(h->h_rank);
+        for (auto &g2 : h->graphs)
+            if (g2.exec) cudaGraphExecDestroy(g2.exec);
         flush_timings(h);
         for (auto e : h->evpool) cudaEventDestroy(e);
     }
@@ -542,6 +898,11 @@ cup_status cup_set_option(cup_handle *h, int option, int64_t value)
         return CUP_OK;
     case CUP_OPT_PROFILE:
         h->profile = (int)value;
+        return CUP_OK;
+    case CUP_OPT_SCHEDULE:
+        if (value < 0 || value > 2) return CUP_ERR_ARG;
+        h->schedule = value ? 1 : 0;
+        h->use_graph = value == 1;
         return CUP_OK;
     default:
         return CUP_ERR_ARG;
@@ -588,6 +949,14 @@ cup_status cup_factor(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t 
     DeviceGuard g(h->device);
     CK(ensure_base(h));
     Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, (cudaStream_t)stream};
+    if (h->schedule == 1) {
+        cup_status s = factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, c.st);
+        if (s != CUP_ERR_SPECULATION_INTERNAL) return s;
+        // a row taken as dependent was not: redo exactly from the saved input
+        CU(cudaMemcpy2DAsync(A, (size_t)lda * 4, h->d_backup, (size_t)n * 4, (size_t)n * 4, (size_t)m,
+                             cudaMemcpyDeviceToDevice, c.st));
+        ++h->stats.host_syncs;
+    }
     int64_t r = 0;
     CK(cup_rec(c, 0, m, 0, &r));
     CK(check_device_error(h, c.st));
@@ -890,6 +1259,22 @@ cup_status cup_trulm(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, uint32_
     CK(ensure_base(h));
     CK(trulm(h, A, lda, n, make_modp(p), h->engine, (cudaStream_t)stream));
     CK(check_device_error(h, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+cup_status cup_factor_batched(cup_handle *h, const cup_batch_item *d_items, int64_t count, int64_t *d_rank,
+                              uint32_t *d_det, void *stream)
+{
+    if (!h || count < 0) return CUP_ERR_ARG;
+    if (count == 0) return CUP_OK;
+    if (!d_items || !d_rank) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (!h->d_next) CU(cudaMalloc(&h->d_next, sizeof(unsigned long long)));
+    int nsm = 0;
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int64_t grid = count < (int64_t)nsm * 2 ? count : (int64_t)nsm * 2;
+    CU(launch_cup_batched(d_items, count, d_rank, d_det, h->d_next, (int)grid, (cudaStream_t)stream));
+    h->stats.launches += 1;
     return CUP_OK;
 }
 

@@ -4,6 +4,62 @@
 #include <cuda_runtime.h>
 #include "modp.cuh"
 
+// A value known on the host or only on the device: s + c0 *p0 + c1 *p1,
+// clamped to [lo, hi]. The device-resident schedule passes the running rank
+// (and the rank at the middle of a node) by pointer; host-driven calls pass
+// constants (p0 = p1 = null). hi is also the host's bound for grid sizes.
+struct Dyn {
+    int64_t s;
+    const int64_t *p0, *p1;
+    int64_t c0, c1;
+    int64_t lo, hi;
+    __host__ __device__ __forceinline__ int64_t eval() const
+    {
+        int64_t v = s;
+        if (p0) v += c0 * *p0;
+        if (p1) v += c1 * *p1;
+        return v < lo ? lo : (v > hi ? hi : v);
+    }
+};
+
+static inline Dyn dconst(int64_t v) { return Dyn{v, nullptr, nullptr, 0, 0, v, v}; }
+static inline Dyn dvar(int64_t s, const int64_t *p0, int64_t c0, const int64_t *p1, int64_t c1, int64_t lo,
+                       int64_t hi)
+{
+    return Dyn{s, p0, p1, c0, c1, lo, hi};
+}
+
+// One Schur update C <- C -/+ A B mod p where the operands are blocks of
+// row-major matrices: element (i, j) of X is X.base[(X.row + i) ld + X.col + j].
+// M is fixed; N and K may be dynamic (K.hi and N.hi bound them).
+struct GemmDesc {
+    const uint32_t *A;
+    int64_t lda;
+    Dyn arow, acol;
+    const uint32_t *B;
+    int64_t ldb;
+    Dyn brow, bcol;
+    uint32_t *C;
+    int64_t ldc;
+    Dyn crow, ccol;
+    int64_t M;
+    Dyn N, K;
+    int add;
+};
+
+// A right-side triangular operation B <- B T^{-1} (or B T) with B rows x n and
+// T n x n (n <= 64) given as blocks of row-major matrices at dynamic offsets.
+struct TriDesc {
+    const uint32_t *T;
+    int64_t ldt;
+    Dyn trow, tcol;
+    uint32_t *B;
+    int64_t ldb;
+    Dyn brow, bcol;
+    int64_t rows;
+    Dyn n;
+};
+
 #define CUP_BMAX 64        // most rows a leaf slab may hold
 #define CUP_WNMAX 128      // widest pivot-search window of a leaf
 #define CUP_NSLOT (CUP_WNMAX + 2)
@@ -32,26 +88,30 @@ struct SlabScratch {
 };
 
 // Kernel launchers (cup_kernels.cu). All are asynchronous on `st`.
-cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, int64_t col0,
-                               int64_t w, int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv,
-                               int64_t *prof, cudaStream_t st);
-cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int64_t col0, int64_t w,
-                               ModP M, const SlabScratch *S, cudaStream_t st);
-cudaError_t launch_swaplist(const int64_t *ipiv, int64_t k0, int64_t k1, int2 *pairs, int *count,
-                            cudaStream_t st);
-cudaError_t launch_laswp(uint32_t *A, int64_t lda, int64_t row0, int64_t nrows, const int2 *pairs,
-                         const int *count, cudaStream_t st);
+#define CUP_DEVERR_SPECULATION 100   // device error word: a row taken as dependent was not
+
+cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, Dyn col0, int64_t n,
+                               int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv, int64_t *prof,
+                               int64_t *rank_next, cudaStream_t st);
+cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, int64_t n, ModP M,
+                               const SlabScratch *S, int *err, cudaStream_t st);
+cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st);
+cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int2 *pairs, const int *count,
+                         cudaStream_t st);
 cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
                                  int64_t m, int n, ModP M, cudaStream_t st);
 cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                                uint32_t *C, int64_t ldc, int64_t Mr, int64_t N, int64_t K, ModP M,
                                cudaStream_t st, int add = 0);
+cudaError_t launch_gemm_cc_desc(const GemmDesc &d, ModP M, cudaStream_t st);
 cudaError_t launch_det_reduce(const uint32_t *A, int64_t lda, int64_t n, const int64_t *ipiv, ModP M,
                               uint32_t *out, cudaStream_t st);
 
 // Tensor-core Schur update (cup_tc.cu).
 int tc_limbs(uint32_t p);
 size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K);
+cudaError_t launch_gemm_tc_desc(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
+                                cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
                                cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
@@ -62,6 +122,8 @@ cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B
 enum { TRI_LEFT = 1, TRI_UPPER = 2, TRI_UNIT = 4, TRI_SOLVE = 8 };
 cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t *B, int64_t ldb,
                             int64_t rows, int64_t cols, ModP M, cudaStream_t st);
+// Right, upper, unit solve on a TriDesc (the TRSM step of the device-resident CUP).
+cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st);
 cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int n, ModP M, cudaStream_t st);
 cudaError_t launch_trulm_leaf(uint32_t *A, int64_t lda, int n, ModP M, cudaStream_t st);
 cudaError_t launch_negate(uint32_t *B, int64_t ldb, int64_t m, int64_t n, uint32_t p, cudaStream_t st);
@@ -77,3 +139,5 @@ cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t 
 
 // Prime check shared by the entry points (cup_api.cu).
 bool cup_internal_prime_ok(uint32_t p);
+
+// Batched CUP (cup_batched.cu).

@@ -70,10 +70,21 @@ __device__ __forceinline__ int window_search(const uint32_t *row, int r, int wne
 
 template <bool MONT>
 __global__ void __launch_bounds__(PIV_THREADS)
-k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, int64_t col0,
-              int64_t w, int wn, int speculate, ModP M, SlabScratch *__restrict__ S,
-              int64_t *__restrict__ g_ipiv, int64_t *__restrict__ g_prof)
+k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const Dyn col0d,
+              int64_t n, int wn, int speculate, ModP M, SlabScratch *__restrict__ S,
+              int64_t *__restrict__ g_ipiv, int64_t *__restrict__ g_prof, int64_t *__restrict__ rank_next)
 {
+    const int64_t col0 = col0d.eval();
+    const int64_t w = n - col0;
+    if (w <= 0) {
+        // every column is already a pivot: the slab's rows are dependent
+        if (threadIdx.x == 0) {
+            S->r_s = 0; S->i_stop = brows; S->wne = 0; S->ext_pos = -1; S->ext_slot = -1;
+            S->n_slot = 0; S->n_spec = 0; S->spec_fail = 0;
+            if (rank_next) *rank_next = col0;
+        }
+        return;
+    }
     extern __shared__ uint32_t W[];            // brows x PIV_LDW window
     __shared__ int s_wcol[CUP_WNMAX];
     __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX], s_spec[CUP_BMAX];
@@ -263,6 +274,7 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
             S->wne = wne;
             S->n_spec = nspec;
             S->spec_fail = 0;
+            if (rank_next) *rank_next = col0 + rs;
         }
     }
     for (int t = tid; t < rs; t += nt) {
@@ -294,9 +306,11 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 // ---------------------------------------------------------------------------
 template <bool WIDE>
 __global__ void __launch_bounds__(256)
-k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int64_t col0, int64_t w, ModP M,
-              SlabScratch *__restrict__ S)
+k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d, int64_t n, ModP M,
+              SlabScratch *__restrict__ S, int *__restrict__ err)
 {
+    const int64_t col0 = col0d.eval();
+    const int64_t w = n - col0;
     __shared__ uint32_t sL[CUP_BMAX][CUP_BMAX + 1];
     __shared__ uint32_t sX[CUP_BMAX][CUP_QT + 1];
     __shared__ uint32_t sPinv[CUP_BMAX];
@@ -389,7 +403,10 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int64_t col0, in
             for (int t = 0; t < rs; ++t) acc_add(acc, (uint64_t)S->Cn[i][t] * sX[t][qq]);
             if (acc_red(acc, M) != x) bad = 1;
         }
-        if (__syncthreads_or(bad) && tid == 0) atomicExch(&S->spec_fail, 1);
+        if (__syncthreads_or(bad) && tid == 0) {
+            atomicExch(&S->spec_fail, 1);
+            if (err) atomicCAS(err, 0, CUP_DEVERR_SPECULATION);
+        }
     }
     // C values for the first tile (positions < r_s <= CUP_QT): sL is free again
     if (q0 == 0) {
@@ -428,9 +445,10 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int64_t col0, in
 // them in sequence (Sec. 1.1: right multiplication by P^T permutes columns).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-k_swaplist(const int64_t *__restrict__ ipiv, int64_t k0, int64_t k1, int2 *__restrict__ pairs,
+k_swaplist(const int64_t *__restrict__ ipiv, const Dyn k0d, const Dyn k1d, int2 *__restrict__ pairs,
            int *__restrict__ count)
 {
+    const int64_t k0 = k0d.eval(), k1 = k1d.eval();
     __shared__ int warp_cnt[32], warp_excl[32];
     __shared__ int chunk_total, base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -466,9 +484,10 @@ k_swaplist(const int64_t *__restrict__ ipiv, int64_t k0, int64_t k1, int2 *__res
 }
 
 __global__ void __launch_bounds__(256)
-k_laswp(uint32_t *__restrict__ A, int64_t lda, int64_t row0, int64_t nrows,
+k_laswp(uint32_t *__restrict__ A, int64_t lda, const Dyn row0d, const Dyn nrowsd,
         const int2 *__restrict__ pairs, const int *__restrict__ count)
 {
+    const int64_t row0 = row0d.eval(), nrows = nrowsd.eval();
     __shared__ int2 sp[256];
     const int n = *count;
     if (n == 0) return;
@@ -544,10 +563,15 @@ k_trsm_ruu_leaf(const uint32_t *__restrict__ U, int64_t ldu, uint32_t *__restric
 #define GB_K 16
 template <bool WIDE>
 __global__ void __launch_bounds__(256)
-k_gemm_sub_cc(const uint32_t *__restrict__ A, int64_t lda, const uint32_t *__restrict__ B,
-              int64_t ldb, uint32_t *__restrict__ C, int64_t ldc, int64_t Mr, int64_t N, int64_t K,
-              ModP Mp, int add)
+k_gemm_sub_cc(const GemmDesc d, ModP Mp)
 {
+    const int64_t Mr = d.M, N = d.N.eval(), K = d.K.eval();
+    if ((int64_t)blockIdx.x * GB_N >= N || K <= 0) return;
+    const int add = d.add;
+    const int64_t lda = d.lda, ldb = d.ldb, ldc = d.ldc;
+    const uint32_t *__restrict__ A = d.A + d.arow.eval() * lda + d.acol.eval();
+    const uint32_t *__restrict__ B = d.B + d.brow.eval() * ldb + d.bcol.eval();
+    uint32_t *__restrict__ C = d.C + d.crow.eval() * ldc + d.ccol.eval();
     __shared__ uint32_t As[GB_K][GB_M + 4];
     __shared__ uint32_t Bs[GB_K][GB_N + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -611,9 +635,9 @@ k_gemm_sub_cc(const uint32_t *__restrict__ A, int64_t lda, const uint32_t *__res
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, int64_t col0,
-                               int64_t w, int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv,
-                               int64_t *prof, cudaStream_t st)
+cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, Dyn col0, int64_t n,
+                               int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv, int64_t *prof,
+                               int64_t *rank_next, cudaStream_t st)
 {
     static bool attr = false;
     // window rows, then a CUP_BMAX^2 temporary used when inverting L
@@ -628,37 +652,39 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
         attr = true;
     }
     if (M.p & 1u)
-        k_slab_pivots<true><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, w, wn, speculate, M, S, ipiv, prof);
+        k_slab_pivots<true><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S, ipiv, prof,
+                                                            rank_next);
     else
-        k_slab_pivots<false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, w, wn, speculate, M, S, ipiv, prof);
+        k_slab_pivots<false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S, ipiv, prof,
+                                                             rank_next);
     return cudaGetLastError();
 }
 
-cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int64_t col0, int64_t w,
-                               ModP M, const SlabScratch *S, cudaStream_t st)
+cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, int64_t n, ModP M,
+                               const SlabScratch *S, int *err, cudaStream_t st)
 {
-    int64_t nb = (w + CUP_QT - 1) / CUP_QT;
+    const int64_t wmax = n - col0.lo;
+    int64_t nb = (wmax + CUP_QT - 1) / CUP_QT;
     if (nb <= 0) return cudaSuccess;
     // CUP_BMAX (p-1)^2 < 2^64 means a row of Minv times a column of X cannot wrap
     // a row of Linv times a column of X sums CUP_BMAX products
     const bool wide = (long double)CUP_BMAX * (M.p - 1) * (long double)(M.p - 1) >= 18446744073709551615.0L;
-    if (wide) k_slab_finish<true><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, w, M, const_cast<SlabScratch *>(S));
-    else k_slab_finish<false><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, w, M, const_cast<SlabScratch *>(S));
+    if (wide) k_slab_finish<true><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err);
+    else k_slab_finish<false><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_swaplist(const int64_t *ipiv, int64_t k0, int64_t k1, int2 *pairs, int *count,
-                            cudaStream_t st)
+cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st)
 {
     k_swaplist<<<1, 1024, 0, st>>>(ipiv, k0, k1, pairs, count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_laswp(uint32_t *A, int64_t lda, int64_t row0, int64_t nrows, const int2 *pairs,
-                         const int *count, cudaStream_t st)
+cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int2 *pairs, const int *count,
+                         cudaStream_t st)
 {
-    if (nrows <= 0) return cudaSuccess;
-    int64_t nb = (nrows + 255) / 256;
+    if (nrows.hi <= 0) return cudaSuccess;
+    int64_t nb = (nrows.hi + 255) / 256;
     k_laswp<<<(unsigned)nb, 256, 0, st>>>(A, lda, row0, nrows, pairs, count);
     return cudaGetLastError();
 }
@@ -675,20 +701,27 @@ cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, in
     return cudaGetLastError();
 }
 
+cudaError_t launch_gemm_cc_desc(const GemmDesc &d, ModP M, cudaStream_t st)
+{
+    if (d.M <= 0 || d.N.hi <= 0 || d.K.hi <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((d.N.hi + GB_N - 1) / GB_N), (unsigned)((d.M + GB_M - 1) / GB_M));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    // K (p-1)^2 < 2^64 means the 64-bit sum of products cannot wrap
+    long double bound = (long double)d.K.hi * (long double)(M.p - 1) * (long double)(M.p - 1);
+    if (bound < 18446744073709551615.0L)
+        k_gemm_sub_cc<false><<<grid, 256, 0, st>>>(d, M);
+    else
+        k_gemm_sub_cc<true><<<grid, 256, 0, st>>>(d, M);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                                uint32_t *C, int64_t ldc, int64_t Mr, int64_t N, int64_t K, ModP M,
                                cudaStream_t st, int add)
 {
-    if (Mr <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((N + GB_N - 1) / GB_N), (unsigned)((Mr + GB_M - 1) / GB_M));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    // K (p-1)^2 < 2^64 means the 64-bit sum of products cannot wrap
-    long double bound = (long double)K * (long double)(M.p - 1) * (long double)(M.p - 1);
-    if (bound < 18446744073709551615.0L)
-        k_gemm_sub_cc<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M, add);
-    else
-        k_gemm_sub_cc<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, Mr, N, K, M, add);
-    return cudaGetLastError();
+    GemmDesc d{A, lda, dconst(0), dconst(0), B, ldb, dconst(0), dconst(0), C, ldc, dconst(0), dconst(0),
+               Mr, dconst(N), dconst(K), add};
+    return launch_gemm_cc_desc(d, M, st);
 }
 
 // ---------------------------------------------------------------------------

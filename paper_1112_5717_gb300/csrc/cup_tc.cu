@@ -170,9 +170,14 @@ struct Cfg {
 template <int L>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            uint32_t *__restrict__ C, int64_t ldc, int M, int N, int Kp, ModP Mp, uint64_t off,
-            uint32_t sh32, int *__restrict__ err, int add)
+            const GemmDesc d, ModP Mp, uint64_t off, uint32_t sh32, int *__restrict__ err)
 {
+    const int M = (int)d.M, N = (int)d.N.eval(), K = (int)d.K.eval();
+    const int Kp = (K + BK - 1) / BK * BK;
+    const int add = d.add;
+    const int64_t ldc = d.ldc;
+    if ((int)blockIdx.x * Cfg<L>::BN >= N || K <= 0) return;       // outside this call's extents
+    uint32_t *C = d.C + d.crow.eval() * ldc + d.ccol.eval();
     using CF = Cfg<L>;
     constexpr int BN = CF::BN, NACC = CF::NACC, NSTAGE = CF::NSTAGE;
     extern __shared__ uint8_t smem_raw[];
@@ -350,54 +355,59 @@ __device__ __forceinline__ void split_digits(uint32_t x, uint32_t p, uint32_t ha
 
 template <int L>
 __global__ void __launch_bounds__(256)
-k_split_rows(const uint32_t *__restrict__ A, int64_t lda, int M, int K, int Kp, uint32_t p,
-             __nv_bfloat16 *__restrict__ out)
+k_split_rows(const GemmDesc d, int Kp_stride, uint32_t p, __nv_bfloat16 *__restrict__ out)
 {
-    // one thread: 8 consecutive k of one row
+    // one thread: 8 consecutive k of one row of A; planes are (L, M, Kp_stride)
+    const int M = (int)d.M, K = (int)d.K.eval();
+    const int Kp = (K + BK - 1) / BK * BK;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int kv = Kp / 8;
+    const int kv = Kp_stride / 8;
     const int64_t i = idx / kv;
     const int k0 = (int)(idx - i * kv) * 8;
-    if (i >= M) return;
+    if (i >= M || k0 >= Kp) return;
+    const uint32_t *A = d.A + (d.arow.eval() + i) * d.lda + d.acol.eval();
     const uint32_t half = (p - 1) / 2;
     __align__(16) __nv_bfloat16 buf[L][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int k = k0 + e;
-        __nv_bfloat16 d[L];
-        split_digits<L>(k < K ? A[i * lda + k] : 0u, p, half, d);
+        __nv_bfloat16 dg[L];
+        split_digits<L>(k < K ? A[k] : 0u, p, half, dg);
 #pragma unroll
-        for (int l = 0; l < L; ++l) buf[l][e] = d[l];
+        for (int l = 0; l < L; ++l) buf[l][e] = dg[l];
     }
-    const int64_t plane = (int64_t)M * Kp;
+    const int64_t plane = (int64_t)M * Kp_stride;
 #pragma unroll
     for (int l = 0; l < L; ++l)
-        *(uint4 *)(out + l * plane + i * Kp + k0) = *(const uint4 *)buf[l];
+        *(uint4 *)(out + l * plane + i * Kp_stride + k0) = *(const uint4 *)buf[l];
 }
 
-// B (K x N) -> planes (L, N, Kp): 32 x 32 tiles through shared memory.
+// B (K x N) -> planes (L, N_stride, Kp_stride): 32 x 32 tiles through shared memory.
 template <int L>
 __global__ void __launch_bounds__(256)
-k_split_cols(const uint32_t *__restrict__ B, int64_t ldb, int K, int N, int Kp, uint32_t p,
-             __nv_bfloat16 *__restrict__ out)
+k_split_cols(const GemmDesc d, int N_stride, int Kp_stride, uint32_t p, __nv_bfloat16 *__restrict__ out)
 {
     __shared__ uint32_t t[32][33];
+    const int K = (int)d.K.eval(), N = (int)d.N.eval();
+    const int Kp = (K + BK - 1) / BK * BK;
     const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    if (k0 >= Kp || n0 >= N) return;
+    const uint32_t *B = d.B + d.brow.eval() * d.ldb + d.bcol.eval();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
     for (int r = ty; r < 32; r += 8) {
         const int k = k0 + r, n = n0 + tx;
-        t[r][tx] = (k < K && n < N) ? B[(int64_t)k * ldb + n] : 0u;
+        t[r][tx] = (k < K && n < N) ? B[(int64_t)k * d.ldb + n] : 0u;
     }
     __syncthreads();
     const uint32_t half = (p - 1) / 2;
-    const int64_t plane = (int64_t)N * Kp;
+    const int64_t plane = (int64_t)N_stride * Kp_stride;
     for (int r = ty; r < 32; r += 8) {
         const int n = n0 + r, k = k0 + tx;
         if (n < N && k < Kp) {
-            __nv_bfloat16 d[L];
-            split_digits<L>(t[tx][r], p, half, d);
+            __nv_bfloat16 dg[L];
+            split_digits<L>(t[tx][r], p, half, dg);
 #pragma unroll
-            for (int l = 0; l < L; ++l) out[l * plane + (int64_t)n * Kp + k] = d[l];
+            for (int l = 0; l < L; ++l) out[l * plane + (int64_t)n * Kp_stride + k] = dg[l];
         }
     }
 }
@@ -431,22 +441,21 @@ bool make_map(CUtensorMap *map, void *base, int kp, int rows, int L, int box_row
 }
 
 template <int L>
-cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C, int64_t ldc,
-                int M, int N, int K, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0,
-                cudaEvent_t ev1, int add)
+cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     using CF = Cfg<L>;
-    const int Kp = (K + BK - 1) / BK * BK;
+    const int M = (int)d.M, Nmax = (int)d.N.hi, Kmax = (int)d.K.hi;
+    const int Kp = (Kmax + BK - 1) / BK * BK;                    // plane row stride
     __nv_bfloat16 *Al = (__nv_bfloat16 *)ws;
     __nv_bfloat16 *Bl = Al + (size_t)L * M * Kp;
     {
         int64_t nthr = (int64_t)M * (Kp / 8);
-        k_split_rows<L><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(A, lda, M, K, Kp, Mp.p, Al);
-        dim3 g((N + 31) / 32, (Kp + 31) / 32);
-        k_split_cols<L><<<g, 256, 0, st>>>(B, ldb, K, N, Kp, Mp.p, Bl);
+        k_split_rows<L><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(d, Kp, Mp.p, Al);
+        dim3 g((Nmax + 31) / 32, (Kp + 31) / 32);
+        k_split_cols<L><<<g, 256, 0, st>>>(d, Nmax, Kp, Mp.p, Bl);
     }
     CUtensorMap ta, tb;
-    if (!make_map(&ta, Al, Kp, M, L, BM) || !make_map(&tb, Bl, Kp, N, L, CF::BN))
+    if (!make_map(&ta, Al, Kp, M, L, BM) || !make_map(&tb, Bl, Kp, Nmax, L, CF::BN))
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -458,9 +467,9 @@ cudaError_t run(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, 
     const int bound_bits = (L <= 3) ? 60 : 52;
     const uint64_t off = ((1ull << bound_bits) / Mp.p + 1) * Mp.p;
     const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
-    dim3 grid((N + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
+    dim3 grid((Nmax + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
     if (ev0) cudaEventRecord(ev0, st);
-    k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, C, ldc, M, N, Kp, Mp, off, sh32, err, add);
+    k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, d, Mp, off, sh32, err);
     cudaError_t e = cudaGetLastError();
     if (ev1) cudaEventRecord(ev1, st);
     return e;
@@ -483,18 +492,26 @@ size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K)
     return (size_t)L * (size_t)(M + N) * (size_t)Kp * 2;
 }
 
+cudaError_t launch_gemm_tc_desc(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0,
+                                cudaEvent_t ev1)
+{
+    if (d.M <= 0 || d.N.hi <= 0 || d.K.hi <= 0) return cudaSuccess;
+    if (d.M > INT32_MAX / 2 || d.N.hi > INT32_MAX / 2 || d.K.hi > INT32_MAX / 2) return cudaErrorInvalidValue;
+    switch (tc_limbs(Mp.p)) {
+    case 1: return tc::run<1>(d, Mp, ws, err, st, ev0, ev1);
+    case 2: return tc::run<2>(d, Mp, ws, err, st, ev0, ev1);
+    case 3: return tc::run<3>(d, Mp, ws, err, st, ev0, ev1);
+    default: return tc::run<4>(d, Mp, ws, err, st, ev0, ev1);
+    }
+}
+
 cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t *C,
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
                                cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, int add)
 {
-    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2) return cudaErrorInvalidValue;
-    switch (tc_limbs(Mp.p)) {
-    case 1: return tc::run<1>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
-    case 2: return tc::run<2>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
-    case 3: return tc::run<3>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
-    default: return tc::run<4>(A, lda, B, ldb, C, ldc, (int)M, (int)N, (int)K, Mp, ws, err, st, ev0, ev1, add);
-    }
+    GemmDesc d{A, lda, dconst(0), dconst(0), B, ldb, dconst(0), dconst(0), C, ldc, dconst(0), dconst(0),
+               M, dconst(N), dconst(K), add};
+    return launch_gemm_tc_desc(d, Mp, ws, err, st, ev0, ev1);
 }
 
 // ---------------------------------------------------------------------------

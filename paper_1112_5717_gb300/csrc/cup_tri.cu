@@ -47,9 +47,13 @@ __device__ void load_tri(const uint32_t *T, int64_t ldt, int n, const ModP &M,
 
 template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
 __global__ void __launch_bounds__(256)
-k_tri_right(const uint32_t *__restrict__ T, int64_t ldt, uint32_t *__restrict__ B, int64_t ldb, int64_t m,
-            int n, ModP M)
+k_tri_right(const TriDesc d, ModP M)
 {
+    const int n = (int)d.n.eval();
+    if (n <= 0) return;
+    const int64_t m = d.rows, ldt = d.ldt, ldb = d.ldb;
+    const uint32_t *__restrict__ T = d.T + d.trow.eval() * ldt + d.tcol.eval();
+    uint32_t *__restrict__ B = d.B + d.brow.eval() * ldb + d.bcol.eval();
     __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
     __shared__ uint32_t sD[TRI_MAX];
     load_tri<UPPER, UNIT, SOLVE, MONT>(T, ldt, n, M, sT, sD);
@@ -149,8 +153,9 @@ static cudaError_t tri_dispatch(bool left, const uint32_t *T, int64_t ldt, uint3
     } else {
         int64_t nb = (rows + 7) / 8;
         if (nb > 152 * 16) nb = 152 * 16;
-        if (mont) k_tri_right<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, rows, n, M);
-        else k_tri_right<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, rows, n, M);
+        TriDesc d{T, ldt, dconst(0), dconst(0), B, ldb, dconst(0), dconst(0), rows, dconst(n)};
+        if (mont) k_tri_right<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, 256, 0, st>>>(d, M);
+        else k_tri_right<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, 256, 0, st>>>(d, M);
     }
     return cudaGetLastError();
 }
@@ -173,6 +178,17 @@ cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t 
                            : tri_dispatch<false, true, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
     return solve ? tri_dispatch<false, false, true>(left, T, ldt, B, ldb, rows, cols, n, M, st)
                  : tri_dispatch<false, false, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
+}
+
+cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
+{
+    if (d.rows <= 0 || d.n.hi <= 0) return cudaSuccess;
+    if (d.n.hi > TRI_MAX) return cudaErrorInvalidValue;
+    int64_t nb = (d.rows + 7) / 8;
+    if (nb > 152 * 16) nb = 152 * 16;
+    if (M.p & 1u) k_tri_right<true, true, true, true><<<(unsigned)nb, 256, 0, st>>>(d, M);
+    else k_tri_right<true, true, true, false><<<(unsigned)nb, 256, 0, st>>>(d, M);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

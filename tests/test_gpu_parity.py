@@ -137,3 +137,38 @@ def test_det(cuda_lib, n, p):
 def test_factor_tensor_engine(cuda_lib, name, tc_min_k):
     A, p = FACTOR_CASES[name]()
     _factor_case(cuda_lib, A, p, engine=1, tc_min_k=tc_min_k)
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+@pytest.mark.parametrize("name", ["dense_plain_512", "rank_def_700x256", "tall_500x90_p3", "zero_40x50"])
+def test_factor_schedules_and_graph_replay(cuda_lib, schedule, name):
+    """Host-driven (0), device-resident replayed as a CUDA graph (1) and
+    device-resident eager (2): three calls on the same buffer each match the oracle."""
+    import torch
+    A, p = FACTOR_CASES[name]()
+    d = oracle.cup_packed(A, p)
+    h = cuda_lib.Handle(engine=1, schedule=schedule)
+    dA = _dev(A)
+    src = dA.clone()
+    stream = torch.cuda.Stream()          # graphs are captured on a stream of our own
+    stream.wait_stream(torch.cuda.current_stream())
+    for call in range(3):
+        with torch.cuda.stream(stream):
+            dA.copy_(src)
+            r, prof, ipiv = h.factor(dA, p)
+        torch.cuda.synchronize()
+        assert r == d["rank"], call
+        assert np.array_equal(prof[:r].cpu().numpy(), d["profile"]), call
+        assert np.array_equal(ipiv[:r].cpu().numpy(), d["ipiv"]), call
+        assert np.array_equal(_host(dA), d["packed"]), call
+    h.close()
+
+
+def test_speculation_fallback_is_exact(cuda_lib):
+    """A window of one position makes the device-resident schedule take rows as
+    dependent that are not; the finish kernel detects it and the call is redone
+    host-driven from the saved input."""
+    p = 251
+    A = _swappy(200, 210, p, seed=77)
+    for window in (1, 2, 4):
+        _factor_case(cuda_lib, A, p, engine=1, leaf_rows=16, window=window, schedule=1)
