@@ -44,13 +44,18 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--p", type=int, default=65521)
+    ap.add_argument("--workload", default="dense_full",
+                    choices=["dense_full", "dense_plain", "rank_deficient", "dense_small_p", "batched"],
+                    help="dense_full (default): 8192^2 GF(65521); dense_plain: 512^2 rank 384; "
+                         "rank_deficient: 16384x4096 rank 3000 GF(8388593); dense_small_p: 32768^2 GF(251); "
+                         "batched: 4096 matrices, 64 primes near 2^30")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--p", type=int, default=None)
     ap.add_argument("--engine", choices=["tensor", "plain"], default="tensor")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-engine comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--cpu-sample", type=int, default=2048, help="side of the oracle's sample matrix")
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="side of the oracle's sample matrix")
     ap.add_argument("--leaf-rows", type=int, default=None)
     ap.add_argument("--window", type=int, default=None)
     ap.add_argument("--tc-min-k", type=int, default=None)
@@ -155,16 +160,59 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# workloads (seeded synthetic inputs of the paper's settings)
+# ---------------------------------------------------------------------------
+def make_workload(args):
+    """Returns (name, list of (matrix, p)) for the chosen workload."""
+    from paper_1112_5717_gb300 import inputs
+    w = args.workload
+    if w == "dense_full":
+        n = args.n or 8192
+        p = args.p or inputs.P_16
+        return f"dense_full {n}x{n} uniform over GF({p})", [(inputs.dense_full(n=n, p=p), p)]
+    if w == "dense_plain":
+        p = args.p or inputs.P_16
+        return f"dense_plain 512x512 rank 384 over GF({p}), rows shuffled", [(inputs.dense_plain(p=p), p)]
+    if w == "rank_deficient":
+        p = args.p or inputs.P_23
+        return (f"rank_deficient 16384x4096 rank 3000 over GF({p}), every 7th row zero, every 5th a combination",
+                [(inputs.rank_deficient(p=p), p)])
+    if w == "dense_small_p":
+        n = args.n or 32768
+        p = args.p or inputs.P_8
+        A = inputs.dense_small_p(n=n, p=p)
+        return f"dense_small_p {n}x{n} uniform over GF({p}) (uint8 input, uint32 in the library)", [(A, p)]
+    mats = inputs.batched()
+    return "batched 4096 matrices, m, n log-uniform in [64, 1024], 64 primes below 2^30", mats
+
+
+# ---------------------------------------------------------------------------
 # the CPU oracle as baseline (test infrastructure, timed as it stands)
 # ---------------------------------------------------------------------------
-def oracle_sample(n: int, p: int):
+def oracle_sample(n: int, p: int, workload: str = "dense_full"):
+    """Times the oracle on one bounded sample of the workload; returns
+    (Gop/s, seconds, threads, description)."""
     import oracle
     from paper_1112_5717_gb300 import inputs
-    A = inputs.dense_full(n=n, p=p, seed=inputs.SEED_BASE + 2)
+    if workload == "batched":
+        mats = inputs.batched(count=64)
+        desc = "CUP of the first 64 matrices of the batched workload"
+    elif workload == "rank_deficient":
+        mats = [(inputs.rank_deficient(m=4 * n, n=n, r=(3 * n) // 4, p=p), p)]
+        desc = f"CUP of one {4 * n}x{n} rank-{(3 * n) // 4} matrix of the rank-deficient structure"
+    elif workload == "dense_plain":
+        mats = [(inputs.dense_plain(p=p), p)]
+        desc = "CUP of the 512x512 rank-384 workload itself"
+    else:
+        mats = [(inputs.dense_full(n=n, p=p, seed=inputs.SEED_BASE + 2), p)]
+        desc = f"CUP of one {n}x{n} uniform matrix over GF({p}) (the workload scaled down)"
     t0 = time.perf_counter()
-    d = oracle.cup(A, p)
+    ops = 0.0
+    for A, q in mats:
+        d = oracle.cup(A, q)
+        ops += cup_ops(A.shape[0], A.shape[1], d["rank"])
     dt = time.perf_counter() - t0
-    return cup_ops(n, n, d["rank"]) / dt / 1e9, dt, oracle.num_threads(), d["rank"]
+    return ops / dt / 1e9, dt, oracle.num_threads(), desc
 
 
 def run_reference(args):
@@ -174,22 +222,21 @@ def run_reference(args):
     import oracle
     oracle.build()
     n = args.cpu_sample
+    p = args.p or 65521
     for _ in range(args.warmup):
-        oracle_sample(n, args.p)
+        oracle_sample(n, p, args.workload)
     vals, times = [], []
     for _ in range(args.steps):
-        v, dt, cores, r = oracle_sample(n, args.p)
+        v, dt, cores, desc = oracle_sample(n, p, args.workload)
         vals.append(v)
         times.append(dt)
     value = statistics.median(vals)
-    sample = (f"CUP of one {n}x{n} uniform matrix over GF({args.p}) per step (the {args.n}x{args.n} "
-              f"workload scaled down), leading-term ops / wall time")
+    sample = f"{desc}, per step; leading-term ops / wall time"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(times) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
            "data": "synthetic",
-           "config": {"workload": f"dense_full {args.n}x{args.n} GF({args.p}) CUP (sampled at {n}x{n} on the host)",
-                      "n": n, "p": args.p},
+           "config": {"workload": f"{args.workload} (sampled on the host: {sample})", "p": p},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -204,7 +251,6 @@ def run_ours(args):
     import torch
 
     import paper_1112_5717_gb300 as cup
-    from paper_1112_5717_gb300 import inputs
 
     world, rank, local = dist_env()
     if world > 1:
@@ -214,32 +260,50 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    n, p = args.n, args.p
     engine = cup.ENGINE_TENSOR if args.engine == "tensor" else cup.ENGINE_PLAIN
+    wname, mats = make_workload(args)
+    batched = args.workload == "batched"
 
-    A_np = inputs.dense_full(n=n, p=p, seed=inputs.SEED_BASE + 2)
-    A_host = torch.from_numpy(A_np.view(np.int32)).pin_memory()
-    A0 = A_host.to(dev)
-    A = torch.empty_like(A0)
+    # pristine inputs resident in HBM (and pinned host copies for the end-to-end leg)
+    hosts = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).pin_memory()
+             for A, _ in mats]
+    primes = [int(q) for _, q in mats]
+    pristine = [t.to(dev) for t in hosts]
+    work = [torch.empty_like(t) for t in pristine]
     opts = {k: v for k, v in (("leaf_rows", args.leaf_rows), ("window", args.window),
                               ("tc_min_k", args.tc_min_k)) if v is not None}
     h = cup.Handle(dev, engine=engine, profile=args.profile, **opts)
-    # a stream of our own: calls repeated on it are replayed as one CUDA graph
+    # a stream of our own (calls repeated on it may be replayed as CUDA graphs)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
 
+    def restore():
+        for w_, p_ in zip(work, pristine):
+            w_.copy_(p_)
+
+    def compute():
+        if batched:
+            ranks, _, _, _ = h.factor_batched(work, primes)
+            return ranks
+        r, _, _ = h.factor(work[0], primes[0])
+        return r
+
     def one_step():
-        A.copy_(A0)
+        restore()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r, prof, ipiv = h.factor(A, p)
+        out = compute()
         e1.record(stream)
-        return r, e0, e1
+        return out, e0, e1
 
     for _ in range(args.warmup):
-        r, _, _ = one_step()
+        out, _, _ = one_step()
     torch.cuda.synchronize()
-    rank_val = r
+    if batched:
+        ranks_v = out.cpu().numpy().tolist()
+    else:
+        ranks_v = [out]
+    ops = sum(cup_ops(A.shape[0], A.shape[1], rr) for (A, _), rr in zip(mats, ranks_v))
     h.reset_stats()
     clocks = ClockSampler(dev)
     clocks.start()
@@ -247,7 +311,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     evs = []
     for _ in range(args.steps):
-        r, e0, e1 = one_step()
+        _, e0, e1 = one_step()
         evs.append((e0, e1))
     torch.cuda.synchronize()
     barrier(world)
@@ -256,20 +320,20 @@ def run_ours(args):
     st = h.stats()
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, world)
-    ops = cup_ops(n, n, rank_val)
     value = ops * world / (ms_max * 1e-3) / 1e9
-
+    shape = {"matrices": len(mats)} if batched else {"m": mats[0][0].shape[0], "n": mats[0][0].shape[1],
+                                                     "p": primes[0], "rank": ranks_v[0]}
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-              "config": {"workload": f"dense_full {n}x{n} uniform over GF({p}), uint32, in-place CUP "
-                                     f"(Algorithm 6) with {args.engine} Schur updates",
-                         "n": n, "p": p, "rank": rank_val, "engine": args.engine,
-                         "limbs": cup_limbs(p) if engine == cup.ENGINE_TENSOR else None,
-                         "l2": "256 MiB input > 129 MiB L2; restored by a device copy before each step",
-                         "parallelism": "replicas" if world > 1 else "single",
-                         "options": opts,
-                         "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
+              "config": dict({"workload": wname + (" (one persistent launch)" if batched else
+                                                   f", in-place CUP (Algorithm 6), {args.engine} Schur updates"),
+                              "engine": args.engine, "leading_term_ops": ops,
+                              "limbs": cup_limbs(primes[0]) if engine == cup.ENGINE_TENSOR else None,
+                              "l2": "inputs restored by a device copy before each step; "
+                                    "the 256 MiB 8192^2 input exceeds the 129 MiB L2",
+                              "parallelism": "replicas" if world > 1 else "single", "options": opts,
+                              "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}, **shape),
               "gpu_launches": int(st["launches"]),
               "clocks": clk}
 
@@ -306,50 +370,51 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
-        out_host = torch.empty_like(A_host).pin_memory()
+        outs = [torch.empty_like(t).pin_memory() for t in hosts]
         e2e_ms = []
         for i in range(max(args.steps, 1) + 1):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            A.copy_(A_host, non_blocking=True)
-            r, prof, ipiv = h.factor(A, p)
-            out_host.copy_(A, non_blocking=True)
-            prof_h = prof.to("cpu", non_blocking=True)
-            ipiv_h = ipiv.to("cpu", non_blocking=True)
+            for w_, t in zip(work, hosts):
+                w_.copy_(t, non_blocking=True)
+            res = compute()
+            for o, w_ in zip(outs, work):
+                o.copy_(w_, non_blocking=True)
+            res_h = res.to("cpu", non_blocking=True) if batched else None
             e1.record(stream)
             torch.cuda.synchronize()
             if i > 0:
                 e2e_ms.append(e0.elapsed_time(e1))
         e_ms = max_over_ranks(statistics.mean(e2e_ms), world)
+        nbytes = sum(t.numel() * 4 for t in hosts)
         result["e2e"] = {"value": ops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
-                         "h2d_bytes_per_step": int(A_host.numel() * 4),
-                         "d2h_bytes_per_step": int(out_host.numel() * 4 + prof_h.numel() * 8 + ipiv_h.numel() * 8)}
+                         "h2d_bytes_per_step": int(nbytes),
+                         "d2h_bytes_per_step": int(nbytes + (res_h.numel() * 8 if batched else 0))}
 
     # the plain CUDA-core INT64 engine on the same workload
-    if not args.no_plain and engine == cup.ENGINE_TENSOR and world == 1:
-        hp = cup.Handle(dev, engine=cup.ENGINE_PLAIN)
-        A.copy_(A0)
-        hp.factor(A, p)
+    if not args.no_plain and engine == cup.ENGINE_TENSOR and world == 1 and not batched:
+        hp = cup.Handle(dev, engine=cup.ENGINE_PLAIN, **opts)
+        restore()
+        hp.factor(work[0], primes[0])
         pm = []
         for _ in range(2):
-            A.copy_(A0)
+            restore()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            hp.factor(A, p)
+            hp.factor(work[0], primes[0])
             e1.record(stream)
             torch.cuda.synchronize()
             pm.append(e0.elapsed_time(e1))
         pms = statistics.mean(pm)
         result["plain"] = {"value": ops / (pms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pms,
-                           "tensor_over_plain": (ops / (ms * 1e-3) / 1e9) / (ops / (pms * 1e-3) / 1e9)}
+                           "tensor_over_plain": pms / ms}
         hp.close()
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, cores, _ = oracle_sample(args.cpu_sample, p)
+        v, dt, cores, desc = oracle_sample(args.cpu_sample, primes[0] if not batched else 0, args.workload)
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                  "sample": f"CUP of one {args.cpu_sample}x{args.cpu_sample} uniform matrix over "
-                                            f"GF({p}) ({dt:.1f} s), leading-term ops / wall time"}
+                                  "sample": f"{desc} ({dt:.1f} s), leading-term ops / wall time"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     h.close()

@@ -130,7 +130,7 @@ cup_status cup_rank_profile(cup_handle *handle, uint32_t *A, int64_t m, int64_t 
                             uint32_t p, int64_t *d_profile, int64_t *rank, void *stream);
 
 /*
- * Determinant of a square matrix (Sec. 5: CUP suffices). A is destroyed.
+ * Determinant of a square matrix (Sec. 4.4: CUP suffices). A is destroyed.
  * *det receives det(A) mod p: 0 if the rank is below n, otherwise the
  * product of C's diagonal (the pivots) times (-1)^(number of nontrivial
  * transpositions).
@@ -140,7 +140,7 @@ cup_status cup_det(cup_handle *handle, uint32_t *A, int64_t n, int64_t lda, uint
 
 /*
  * In-place inverse of a square matrix (Algorithm 8 via Algorithm 7 and the
- * TRSM/TRTRI/TRULM building blocks, Sec. 3.5 and Sec. 4.3). On success A
+ * TRSM/TRTRI/TRULM building blocks, Sec. 3.4, 3.5 and 4.3). On success A
  * holds A^{-1}. Returns CUP_SINGULAR (A holds the [C\U] factors) if the rank
  * is below n.
  */
@@ -158,7 +158,7 @@ cup_status cup_rref(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64
                     int64_t *d_profile, int64_t *rank, uint32_t *X, int64_t ldx, void *stream);
 
 /*
- * Linear system A X = B (Sec. 5: solving reduces to CUP). A (m x n) is
+ * Linear system A X = B (Sec. 4.4: solving reduces to CUP). A (m x n) is
  * destroyed; B (m x k, ldb) is read and destroyed; X (n x k, ldx) receives
  * the solution whose entries outside the CUP pivot columns are zero
  * (x = P^T [U1^{-1} L1^{-1} b_profile; 0]). Returns CUP_INCONSISTENT when no

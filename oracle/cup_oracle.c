@@ -333,7 +333,7 @@ int cupo_inverse(const u32 *A, i64 n, i64 lda, u32 p, u32 *Ainv, i64 ldi)
 
 /*
  * Particular solution of A x = B (A m x n, B m x k, X n x k) whose entries
- * outside the pivot columns of the CUP decomposition are zero (Sec. 5 lists
+ * outside the pivot columns of the CUP decomposition are zero (Sec. 4.4 lists
  * system solving among the problems reduced to CUP; the paper does not fix a
  * particular solution, this choice is the one a CUP-based solver produces).
  * The pivot column set S is read from `ipiv` (r transpositions, as returned by

@@ -727,7 +727,7 @@ cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B
 // ---------------------------------------------------------------------------
 // Determinant from a full-rank CUP: the product of C's diagonal (the pivots,
 // stored on A's diagonal by [C\U]) times (-1)^(number of nontrivial
-// transpositions) (Sec. 5; for rank n the profile is 0..n-1, so pivot t sits
+// transpositions) (Sec. 4.4; for rank n the profile is 0..n-1, so pivot t sits
 // at (t, t)). One CTA, tree product modulo p.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
