@@ -288,14 +288,15 @@ cup_status trsm_ruu(cup_handle *h, const uint32_t *U, int64_t ldu, uint32_t *B, 
                     int64_t m, int64_t n, const ModP &M, int engine, cudaStream_t st)
 {
     if (m <= 0 || n <= 0) return CUP_OK;
-    if (n <= 64) {
+    if (n <= 128) {
         ClassTimer tm(h, st, 4);
-        CU(launch_trsm_ruu_leaf(U, ldu, B, ldb, m, (int)n, M, st));
+        TriDesc d{U, ldu, dconst(0), dconst(0), B, ldb, dconst(0), dconst(0), m, dconst(n)};
+        CU(launch_trsm_ruu_desc(d, M, st));
         h->stats.launches += 1;
         return CUP_OK;
     }
     // Algorithm 2: B1 <- B1 U1^{-1}; B2 <- B2 - B1 V; B2 <- B2 U2^{-1}
-    int64_t k = ((n / 2) + 63) / 64 * 64;
+    int64_t k = ((n / 2) + 127) / 128 * 128;
     CK(trsm_ruu(h, U, ldu, B, ldb, m, k, M, engine, st));
     CK(mm_sub(h, B + k, ldb, B, ldb, U + k, ldu, m, n - k, k, M, engine, st));
     CK(trsm_ruu(h, U + k * ldu + k, ldu, B + k, ldb, m, n - k, M, engine, st));
@@ -548,9 +549,8 @@ cup_status dev_laswp(DevCtx &c, Dyn row0, Dyn nrows, Dyn k0, Dyn k1)
     cup_handle *h = c.h;
     if (nrows.hi <= 0 || k1.hi <= k0.lo) return CUP_OK;
     ClassTimer tm(h, c.st, 5);
-    CU(launch_swaplist(c.ipiv, k0, k1, h->d_pairs, h->d_count, c.st));
-    CU(launch_laswp(c.A, c.lda, row0, nrows, h->d_pairs, h->d_count, c.st));
-    h->stats.launches += 2;
+    CU(launch_laswp_fused(c.A, c.lda, row0, nrows, c.ipiv, k0, k1, c.st));
+    h->stats.launches += 1;
     return CUP_OK;
 }
 
@@ -562,7 +562,7 @@ cup_status dev_trsm(DevCtx &c, const int64_t *col0p, const int64_t *midp, int64_
 {
     cup_handle *h = c.h;
     if (len <= 0) return CUP_OK;
-    if (len <= 64) {
+    if (len <= 128) {
         TriDesc d{c.A, c.lda, dvar(j0, col0p, 1, nullptr, 0, 0, c.n), dvar(j0, col0p, 1, nullptr, 0, 0, c.n),
                   c.A, c.lda, dconst(a2), dvar(j0, col0p, 1, nullptr, 0, 0, c.n), m2,
                   dvar(-j0, midp, 1, col0p, -1, 0, len)};
@@ -571,7 +571,7 @@ cup_status dev_trsm(DevCtx &c, const int64_t *col0p, const int64_t *midp, int64_
         h->stats.launches += 1;
         return CUP_OK;
     }
-    const int64_t k = ((len / 2) + 63) / 64 * 64;
+    const int64_t k = ((len / 2) + 127) / 128 * 128;
     CK(dev_trsm(c, col0p, midp, a2, m2, j0, k));
     GemmDesc g{c.A, c.lda, dconst(a2), dvar(j0, col0p, 1, nullptr, 0, 0, c.n),
                c.A, c.lda, dvar(j0, col0p, 1, nullptr, 0, 0, c.n), dvar(j0 + k, col0p, 1, nullptr, 0, 0, c.n),

@@ -22,6 +22,21 @@ struct Dyn {
     }
 };
 
+#ifdef __CUDACC__
+// Asynchronous 4-byte global -> shared copies (no register staging, so every
+// copy of a tile is in flight at once); cp_async_wait_all() waits for this
+// thread's copies, a __syncthreads() after it publishes them to the block.
+__device__ __forceinline__ void cp_async4(uint32_t *smem, const uint32_t *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+#endif
+
 static inline Dyn dconst(int64_t v) { return Dyn{v, nullptr, nullptr, 0, 0, v, v}; }
 static inline Dyn dvar(int64_t s, const int64_t *p0, int64_t c0, const int64_t *p1, int64_t c1, int64_t lo,
                        int64_t hi)
@@ -98,6 +113,8 @@ cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, in
 cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st);
 cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int2 *pairs, const int *count,
                          cudaStream_t st);
+cudaError_t launch_laswp_fused(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int64_t *ipiv, Dyn k0, Dyn k1,
+                               cudaStream_t st);
 cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
                                  int64_t m, int n, ModP M, cudaStream_t st);
 cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,

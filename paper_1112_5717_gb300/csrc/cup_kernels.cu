@@ -32,7 +32,7 @@
 // to the remaining rows (TRSM + MM, as at an internal node of Algorithm 6) and
 // calls the kernel again on them.
 // ---------------------------------------------------------------------------
-#define PIV_THREADS 512
+#define PIV_THREADS 256
 #define PIV_LDW (CUP_WNMAX + 1)
 
 // One fraction-free update f x - m y, scaled by R^{-1} in the Montgomery
@@ -97,10 +97,12 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     const int wne = (int)(w < (int64_t)wn ? w : (int64_t)wn);
     const uint32_t one = 1u % M.p;
 
-    for (int idx = tid; idx < brows * wne; idx += nt) {
-        int i = idx / wne, q = idx - i * wne;
-        W[i * PIV_LDW + q] = A[(a + i) * lda + col0 + q];
+    // window: every element copied asynchronously, one memory latency for the tile
+    for (int i = warp; i < brows; i += nt >> 5) {
+        const uint32_t *src = A + (a + i) * lda + col0;
+        for (int q = lane; q < wne; q += 32) cp_async4(W + i * PIV_LDW + q, src + q);
     }
+    cp_async_wait_all();
     for (int q = tid; q < wne; q += nt) s_wcol[q] = q;
     if (tid == 0) s_ext = -1;
     __syncthreads();
@@ -144,17 +146,30 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         }
         const uint32_t f = W[i * PIV_LDW + r];
         if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
-        // rows below, window positions (r, wne): one column per thread slot,
-        // the pivot-row entry kept in a register
+        // rows below, window positions (r, wne): lanes take rows i+1+lane and
+        // i+33+lane (their multipliers in registers), warps take columns; the
+        // pivot-row entry of a column is one broadcast read
         {
-            const int nq = wne - r - 1;
-            const int cx = tid & 127, ry = tid >> 7, nry = nt >> 7;
-            if (cx < nq) {
-                const int q = r + 1 + cx;
-                const uint32_t y = W[i * PIV_LDW + q];
-                for (int ii = i + 1 + ry; ii < brows; ii += nry) {
-                    uint32_t *wr = W + ii * PIV_LDW;
-                    wr[q] = ff<MONT>(f, wr[q], wr[r], y, M);
+            const uint32_t *prow = W + i * PIV_LDW;
+            const int ra = i + 1 + lane, rb = i + 33 + lane;
+            const bool va = ra < brows, vb = rb < brows;
+            uint32_t *wa = W + (va ? ra : 0) * PIV_LDW, *wb = W + (vb ? rb : 0) * PIV_LDW;
+            const uint32_t ma = va ? wa[r] : 0u, mb = vb ? wb[r] : 0u;
+            const int nw = nt >> 5;
+            if (i + 1 < brows) {
+                int q = r + 1 + warp;
+                for (; q + nw < wne; q += 2 * nw) {
+                    const uint32_t y0 = prow[q], y1 = prow[q + nw];
+                    uint32_t a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;
+                    if (va) { a0 = wa[q]; a1 = wa[q + nw]; }
+                    if (vb) { b0 = wb[q]; b1 = wb[q + nw]; }
+                    if (va) { wa[q] = ff<MONT>(f, a0, ma, y0, M); wa[q + nw] = ff<MONT>(f, a1, ma, y1, M); }
+                    if (vb) { wb[q] = ff<MONT>(f, b0, mb, y0, M); wb[q + nw] = ff<MONT>(f, b1, mb, y1, M); }
+                }
+                if (q < wne) {
+                    const uint32_t y0 = prow[q];
+                    if (va) wa[q] = ff<MONT>(f, wa[q], ma, y0, M);
+                    if (vb) wb[q] = ff<MONT>(f, wb[q], mb, y0, M);
                 }
             }
         }
@@ -319,7 +334,7 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
     const int rs = S->r_s, stop = S->i_stop, wne = S->wne;
     const int64_t q0 = (int64_t)blockIdx.x * CUP_QT;
     if (q0 >= w) return;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
     const int ext_pos = S->ext_pos, ext_slot = S->ext_slot;
 
@@ -334,18 +349,25 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
         sSlot[qq] = slot;
     }
     __syncthreads();
-    for (int idx = tid; idx < CUP_BMAX * CUP_BMAX; idx += nt) {
-        int t = idx / CUP_BMAX, u = idx - t * CUP_BMAX;
-        sL[t][u] = (t < rs && u < rs) ? S->Linv[t][u] : 0u;
-    }
-    for (int idx = tid; idx < CUP_BMAX * CUP_QT; idx += nt) {
-        int t = idx / CUP_QT, qq = idx - t * CUP_QT;
-        uint32_t v = 0u;
-        if (t < rs && qq < nq) {
-            int slot = sSlot[qq];
-            v = (slot >= 0) ? S->Dorig[slot][sProf[t]] : A[(a + sProf[t]) * lda + col0 + sOrig[qq]];
+    {
+        // 16 independent loads in flight per thread for Linv and for X
+        const int u = tid & 63, t0 = tid >> 6;          // 4 row groups
+        uint32_t lv[16], xv[16];
+        const int slot = sSlot[u];
+        const int orig = sOrig[u];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int t = t0 + 4 * k;
+            lv[k] = (t < rs && u < rs) ? S->Linv[t][u] : 0u;
+            xv[k] = 0u;
+            if (t < rs && u < nq)
+                xv[k] = (slot >= 0) ? S->Dorig[slot][sProf[t]] : A[(a + sProf[t]) * lda + col0 + orig];
         }
-        sX[t][qq] = v;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            sL[t0 + 4 * k][u] = lv[k];
+            sX[t0 + 4 * k][u] = xv[k];
+        }
     }
     __syncthreads();
     // U tile = Linv X: each thread a 4 x 4 block (rows ty + 16 i, columns tx + 16 j)
@@ -411,16 +433,20 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
     // C values for the first tile (positions < r_s <= CUP_QT): sL is free again
     if (q0 == 0) {
         __syncthreads();
-        for (int idx = tid; idx < stop * rs; idx += nt) {
-            int i = idx / rs, t = idx - i * rs;
-            sL[i][t] = S->Cn[i][t];
-        }
+        const int t = tid & 63, i0 = tid >> 6;
+        uint32_t cv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) cv[k] = (i0 + 4 * k < stop && t < rs) ? S->Cn[i0 + 4 * k][t] : 0u;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (i0 + 4 * k < stop && t < rs) sL[i0 + 4 * k][t] = cv[k];
     }
     __syncthreads();
     // rows: U rows col0 + t (t < rs), then slab rows a + i (i < stop) that are not U rows
     const int nrow = rs + stop;
-    for (int idx = tid; idx < nrow * nq; idx += nt) {
-        int k = idx / nq, qq = idx - k * nq;
+    const int qq = tid & (CUP_QT - 1);
+    for (int k = tid >> 6; k < nrow; k += nt >> 6) {
+        if (qq >= nq) continue;
         int64_t q = q0 + qq;
         int64_t rho;
         uint32_t v;
@@ -506,6 +532,47 @@ k_laswp(uint32_t *__restrict__ A, int64_t lda, const Dyn row0d, const Dyn nrowsd
                 row[pr.y] = x;
             }
         }
+    }
+}
+
+// Transpositions (t, ipiv[t]) for t in [k0, k1), compacted to the nontrivial
+// ones by every CTA itself (in order, a chunk of 256 at a time), then applied
+// to this CTA's rows: one launch, no separate list.
+__global__ void __launch_bounds__(256)
+k_laswp_fused(uint32_t *__restrict__ A, int64_t lda, const Dyn row0d, const Dyn nrowsd,
+              const int64_t *__restrict__ ipiv, const Dyn k0d, const Dyn k1d)
+{
+    const int64_t row0 = row0d.eval(), nrows = nrowsd.eval();
+    const int64_t k0 = k0d.eval(), k1 = k1d.eval();
+    if (k1 <= k0 || nrows <= 0 || (int64_t)blockIdx.x * blockDim.x >= nrows) return;
+    __shared__ int2 sp[256];
+    __shared__ int wcnt[8], wex[8], tot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
+    uint32_t *row = A + (row0 + i) * lda;
+    for (int64_t c0 = k0; c0 < k1; c0 += 256) {
+        const int64_t t = c0 + tid;
+        const int64_t c = (t < k1) ? ipiv[t] : t;
+        const bool nz = (t < k1) && (c != t);
+        const unsigned bal = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int w = 0; w < 8; ++w) { wex[w] = acc; acc += wcnt[w]; }
+            tot = acc;
+        }
+        __syncthreads();
+        if (nz) sp[wex[warp] + __popc(bal & ((1u << lane) - 1u))] = make_int2((int)t, (int)c);
+        __syncthreads();
+        if (i < nrows)
+            for (int k = 0; k < tot; ++k) {
+                const int2 pr = sp[k];
+                const uint32_t x = row[pr.x];
+                row[pr.x] = row[pr.y];
+                row[pr.y] = x;
+            }
+        __syncthreads();
     }
 }
 
@@ -686,6 +753,15 @@ cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const in
     if (nrows.hi <= 0) return cudaSuccess;
     int64_t nb = (nrows.hi + 255) / 256;
     k_laswp<<<(unsigned)nb, 256, 0, st>>>(A, lda, row0, nrows, pairs, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_laswp_fused(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int64_t *ipiv, Dyn k0, Dyn k1,
+                               cudaStream_t st)
+{
+    if (nrows.hi <= 0 || k1.hi <= k0.lo) return cudaSuccess;
+    int64_t nb = (nrows.hi + 255) / 256;
+    k_laswp_fused<<<(unsigned)nb, 256, 0, st>>>(A, lda, row0, nrows, ipiv, k0, k1);
     return cudaGetLastError();
 }
 

@@ -30,10 +30,20 @@ template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
 __device__ void load_tri(const uint32_t *T, int64_t ldt, int n, const ModP &M,
                          uint32_t (*sT)[TRI_MAX + 1], uint32_t *sD)
 {
-    for (int idx = threadIdx.x; idx < TRI_MAX * TRI_MAX; idx += blockDim.x) {
-        const int k = idx / TRI_MAX, j = idx - k * TRI_MAX;
-        const bool in = (k < n && j < n) && (UPPER ? (j > k) : (j < k));
-        sT[k][j] = to_mont<MONT>(in ? T[k * ldt + j] : 0u, M);
+    for (int base = threadIdx.x; base < TRI_MAX * TRI_MAX; base += 8 * blockDim.x) {
+        uint32_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = base + e * blockDim.x;
+            const int k = idx / TRI_MAX, j = idx - k * TRI_MAX;
+            const bool in = idx < TRI_MAX * TRI_MAX && (k < n && j < n) && (UPPER ? (j > k) : (j < k));
+            v[e] = in ? T[k * ldt + j] : 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = base + e * blockDim.x;
+            if (idx < TRI_MAX * TRI_MAX) sT[idx / TRI_MAX][idx % TRI_MAX] = to_mont<MONT>(v[e], M);
+        }
     }
     for (int k = threadIdx.x; k < TRI_MAX; k += blockDim.x) {
         uint32_t d = 1u % M.p;
@@ -180,14 +190,75 @@ cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t 
                  : tri_dispatch<false, false, false>(left, T, ldt, B, ldb, rows, cols, n, M, st);
 }
 
+// TRSM(Right, Upper, Unit) on blocks of up to 128 columns (the TRSM step of
+// Algorithm 6): one warp per row of B, each lane holding columns lane + 32 k;
+// at step k the final x_k is broadcast and the later columns subtract x_k u_kj.
+#define RUU_MAX 128
+#define RUU_LDS (RUU_MAX + 1)
+template <bool MONT>
+__global__ void __launch_bounds__(256)
+k_trsm_ruu128(const TriDesc d, ModP M)
+{
+    extern __shared__ uint32_t sU[];                      // RUU_MAX x RUU_LDS, Montgomery form
+    const int n = (int)d.n.eval();
+    if (n <= 0) return;
+    const int64_t m = d.rows, ldt = d.ldt, ldb = d.ldb;
+    const uint32_t *__restrict__ T = d.T + d.trow.eval() * ldt + d.tcol.eval();
+    uint32_t *__restrict__ B = d.B + d.brow.eval() * ldb + d.bcol.eval();
+    // strictly upper part of the n x n block by asynchronous copies, zeros elsewhere
+    // (rows >= n are never read); then the copied entries to Montgomery form
+    for (int idx = threadIdx.x; idx < n * RUU_MAX; idx += blockDim.x) {
+        const int k = idx >> 7, j = idx & (RUU_MAX - 1);
+        if (j > k && j < n) cp_async4(sU + k * RUU_LDS + j, T + k * ldt + j);
+        else sU[k * RUU_LDS + j] = 0u;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (MONT)
+        for (int idx = threadIdx.x; idx < n * RUU_MAX; idx += blockDim.x) {
+            const int k = idx >> 7, j = idx & (RUU_MAX - 1);
+            if (j > k && j < n) sU[k * RUU_LDS + j] = to_mont<MONT>(sU[k * RUU_LDS + j], M);
+        }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nw) {
+        uint32_t *row = B + i * ldb;
+        uint32_t x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = (lane + 32 * c < n) ? row[lane + 32 * c] : 0u;
+        for (int k = 0; k < n; ++k) {
+            const uint32_t src = (k < 32) ? x[0] : (k < 64) ? x[1] : (k < 96) ? x[2] : x[3];
+            const uint32_t xk = __shfl_sync(0xffffffffu, src, k & 31);
+            if (xk) {
+                const uint32_t *uk = sU + k * RUU_LDS + lane;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) x[c] = subm(x[c], mmul<MONT>(xk, uk[32 * c], M), M);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (lane + 32 * c < n) row[lane + 32 * c] = x[c];
+    }
+}
+
 cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
 {
     if (d.rows <= 0 || d.n.hi <= 0) return cudaSuccess;
-    if (d.n.hi > TRI_MAX) return cudaErrorInvalidValue;
+    if (d.n.hi > RUU_MAX) return cudaErrorInvalidValue;
+    static bool attr = false;
+    const size_t smem = (size_t)RUU_MAX * RUU_LDS * sizeof(uint32_t);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsm_ruu128<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     int64_t nb = (d.rows + 7) / 8;
-    if (nb > 152 * 16) nb = 152 * 16;
-    if (M.p & 1u) k_tri_right<true, true, true, true><<<(unsigned)nb, 256, 0, st>>>(d, M);
-    else k_tri_right<true, true, true, false><<<(unsigned)nb, 256, 0, st>>>(d, M);
+    if (nb > 152 * 8) nb = 152 * 8;
+    if (M.p & 1u) k_trsm_ruu128<true><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    else k_trsm_ruu128<false><<<(unsigned)nb, 256, smem, st>>>(d, M);
     return cudaGetLastError();
 }
 
