@@ -195,7 +195,17 @@ cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t 
 // at step k the final x_k is broadcast and the later columns subtract x_k u_kj.
 #define RUU_MAX 128
 #define RUU_LDS (RUU_MAX + 1)
-template <bool MONT>
+// Montgomery reduction of T < 2 p R (p < 2^24) to [0, p): the raw result is below 3p.
+__device__ __forceinline__ uint32_t redc_lazy(uint64_t T, const ModP &M)
+{
+    const uint32_t m = (uint32_t)T * M.pneg;
+    uint32_t t = (uint32_t)((T + (uint64_t)m * M.p) >> 32);
+    if (t >= M.p) t -= M.p;
+    if (t >= M.p) t -= M.p;
+    return t;
+}
+
+template <bool MONT, bool LAZY>
 __global__ void __launch_bounds__(256)
 k_trsm_ruu128(const TriDesc d, ModP M)
 {
@@ -224,21 +234,49 @@ k_trsm_ruu128(const TriDesc d, ModP M)
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nw) {
         uint32_t *row = B + i * ldb;
-        uint32_t x[4];
+        if (LAZY) {
+            // x_j = b_j - sum_{k<j} x_k u_kj accumulated unreduced as R b_j + sum (p - x_k) (R u_kj):
+            // only column k is reduced at step k (one Montgomery reduction on the chain).
+            // With p < 2^24 the sum stays below p R + 128 p^2 < 2 p R, so the
+            // reduction lands in [0, 3p).
+            uint64_t acc[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) x[c] = (lane + 32 * c < n) ? row[lane + 32 * c] : 0u;
-        for (int k = 0; k < n; ++k) {
-            const uint32_t src = (k < 32) ? x[0] : (k < 64) ? x[1] : (k < 96) ? x[2] : x[3];
-            const uint32_t xk = __shfl_sync(0xffffffffu, src, k & 31);
-            if (xk) {
-                const uint32_t *uk = sU + k * RUU_LDS + lane;
+            for (int c = 0; c < 4; ++c)
+                acc[c] = (lane + 32 * c < n) ? ((uint64_t)row[lane + 32 * c] << 32) : 0ull;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) x[c] = subm(x[c], mmul<MONT>(xk, uk[32 * c], M), M);
+            for (int cb = 0; cb < 4; ++cb) {
+                if (32 * cb >= n) break;
+                const int kend = n - 32 * cb < 32 ? n - 32 * cb : 32;
+                for (int kk = 0; kk < kend; ++kk) {
+                    const int k = 32 * cb + kk;
+                    uint32_t t = redc_lazy(acc[cb], M);
+                    const uint32_t xk = __shfl_sync(0xffffffffu, t, kk);
+                    const uint32_t nx = xk ? M.p - xk : 0u;
+                    const uint32_t *uk = sU + k * RUU_LDS + lane;
+#pragma unroll
+                    for (int c = cb; c < 4; ++c) acc[c] += (uint64_t)nx * uk[32 * c];
+                }
             }
-        }
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (lane + 32 * c < n) row[lane + 32 * c] = x[c];
+            for (int c = 0; c < 4; ++c)
+                if (lane + 32 * c < n) row[lane + 32 * c] = redc_lazy(acc[c], M);
+        } else {
+            uint32_t x[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[c] = (lane + 32 * c < n) ? row[lane + 32 * c] : 0u;
+            for (int k = 0; k < n; ++k) {
+                const uint32_t src = (k < 32) ? x[0] : (k < 64) ? x[1] : (k < 96) ? x[2] : x[3];
+                const uint32_t xk = __shfl_sync(0xffffffffu, src, k & 31);
+                if (xk) {
+                    const uint32_t *uk = sU + k * RUU_LDS + lane;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) x[c] = subm(x[c], mmul<MONT>(xk, uk[32 * c], M), M);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (lane + 32 * c < n) row[lane + 32 * c] = x[c];
+        }
     }
 }
 
@@ -249,16 +287,19 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
     static bool attr = false;
     const size_t smem = (size_t)RUU_MAX * RUU_LDS * sizeof(uint32_t);
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm_ruu128<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(k_trsm_ruu128<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsm_ruu128<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     int64_t nb = (d.rows + 7) / 8;
     if (nb > 152 * 8) nb = 152 * 8;
-    if (M.p & 1u) k_trsm_ruu128<true><<<(unsigned)nb, 256, smem, st>>>(d, M);
-    else k_trsm_ruu128<false><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    if ((M.p & 1u) && M.p < (1u << 24)) k_trsm_ruu128<true, true><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    else if (M.p & 1u) k_trsm_ruu128<true, false><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    else k_trsm_ruu128<false, false><<<(unsigned)nb, 256, smem, st>>>(d, M);
     return cudaGetLastError();
 }
 
