@@ -21,9 +21,13 @@
 // Leaf slab, pivot phase (one CTA).
 //
 // Window: positions [0, wne) of the slab rows [a, a + brows), columns
-// [col0, col0 + w). The window is eliminated eagerly; the columns T of a
-// row-operation matrix (T * slab = eliminated slab) are carried alongside, so
-// that U's rows over the whole width are Minv * (pivot rows of the slab),
+// [col0, col0 + w). The window is eliminated in panels of PIV_PB rows: the
+// panel's rows are taken one by one (each step updating only the panel), then
+// every row below takes the panel's pivots in one fused update whose
+// coefficients come from unrolling the fraction-free recurrence, so no field
+// inversion is needed there either. The row-operation matrix E (eliminated
+// slab = E * slab) is carried alongside; its pivot block gives L^{-1}, so
+// that U's rows over the whole width are L^{-1} * (pivot rows of the slab),
 // which the finish kernel evaluates as a small matrix product.
 //
 // A row whose window residual is zero while pivots already exist in this slab
@@ -32,8 +36,15 @@
 // to the remaining rows (TRSM + MM, as at an internal node of Algorithm 6) and
 // calls the kernel again on them.
 // ---------------------------------------------------------------------------
-#define PIV_THREADS 256
+#ifndef PIV_THREADS
+
+#define PIV_THREADS 512
+#endif
 #define PIV_LDW (CUP_WNMAX + 1)
+#define PIV_LDE (CUP_BMAX + 1)
+#ifndef PIV_PB
+#define PIV_PB 8                    // panel rows of the blocked window elimination
+#endif
 
 // One fraction-free update f x - m y, scaled by R^{-1} in the Montgomery
 // variant (odd p): the common factor only changes the tracked row scales.
@@ -68,7 +79,7 @@ __device__ __forceinline__ int window_search(const uint32_t *row, int r, int wne
     return -1;
 }
 
-template <bool MONT>
+template <bool MONT, bool WIDE>
 __global__ void __launch_bounds__(PIV_THREADS)
 k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const Dyn col0d,
               int64_t n, int wn, int speculate, ModP M, SlabScratch *__restrict__ S,
@@ -85,22 +96,30 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         }
         return;
     }
-    extern __shared__ uint32_t W[];            // brows x PIV_LDW window
+    extern __shared__ uint32_t W[];            // brows x PIV_LDW window, then the row-operation matrix
+    uint32_t *const E = W + CUP_BMAX * PIV_LDW; // E (CUP_BMAX x PIV_LDE): eliminated slab = E * slab
     __shared__ int s_wcol[CUP_WNMAX];
     __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX], s_spec[CUP_BMAX];
     __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_muinv[CUP_BMAX], s_Sinv[CUP_BMAX],
         s_Sfwd[CUP_BMAX];
+    __shared__ uint32_t s_coef[CUP_BMAX][PIV_PB + 1];   // -a_kt of the block update, per row below a panel
     __shared__ int s_c, s_ext;
     __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
 
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int wne = (int)(w < (int64_t)wn ? w : (int64_t)wn);
     const uint32_t one = 1u % M.p;
+    // R^{-1} for the Montgomery variant (the factor each fraction-free update carries), else 1
+    const uint32_t rinv = MONT ? redc(1ull, M) : one;
 
     // window: every element copied asynchronously, one memory latency for the tile
-    for (int i = warp; i < brows; i += nt >> 5) {
+    for (int i = warp; i < brows; i += nw) {
         const uint32_t *src = A + (a + i) * lda + col0;
         for (int q = lane; q < wne; q += 32) cp_async4(W + i * PIV_LDW + q, src + q);
+    }
+    for (int idx = tid; idx < brows * CUP_BMAX; idx += nt) {
+        const int i = idx >> 6, j = idx & (CUP_BMAX - 1);
+        E[i * PIV_LDE + j] = (i == j) ? one : 0u;
     }
     cp_async_wait_all();
     for (int q = tid; q < wne; q += nt) s_wcol[q] = q;
@@ -108,74 +127,166 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     __syncthreads();
 
     int r = 0, stop = brows, nspec = 0;
+    bool done = false;
     uint32_t Sprod = one;                      // product of the row scales applied so far
-    for (int i = 0; i < brows; ++i) {
-        if ((int64_t)r >= w) break;            // every column is a pivot: later rows are dependent
-        int c = window_search(W + i * PIV_LDW, r, wne, lane);
-        if (c < 0) {
-            if ((int64_t)wne == w) continue;   // whole residual known and zero
-            if (r != 0) {
-                if (!speculate) { stop = i; break; }
-                if (tid == 0) s_spec[nspec] = i;   // verified by the finish kernel
-                ++nspec;
-                continue;
+    for (int p0 = 0; p0 < brows && !done; p0 += PIV_PB) {
+        // Panel of rows [p0, pend): the rows are taken one by one as in the
+        // unblocked elimination, but each step only updates the panel's rows.
+        const int pend = p0 + PIV_PB < brows ? p0 + PIV_PB : brows;
+        const int r0 = r;
+        int lim = brows;                       // rows that still need this panel's pivots
+        for (int i = p0; i < pend; ++i) {
+            if ((int64_t)r >= w) { done = true; break; }   // every column is a pivot: later rows are dependent
+            int c = window_search(W + i * PIV_LDW, r, wne, lane);
+            if (c < 0) {
+                if ((int64_t)wne == w) continue;   // whole residual known and zero
+                if (r != 0) {
+                    if (!speculate) { stop = i; lim = i; done = true; break; }
+                    if (tid == 0) s_spec[nspec] = i;   // verified by the finish kernel
+                    ++nspec;
+                    continue;
+                }
+                // No pivot yet in this slab: row i of A is still the unreduced,
+                // unpermuted input, so its first nonzero beyond the window is read directly.
+                if (tid == 0) s_c = INT_MAX;
+                __syncthreads();
+                const uint32_t *row = A + (a + i) * lda + col0;
+                for (int64_t q = wne + tid; q < w; q += nt)
+                    if (row[q]) { atomicMin(&s_c, (int)q); break; }
+                __syncthreads();
+                c = s_c;
+                __syncthreads();
+                if (c == INT_MAX) continue;        // zero row
+                for (int ii = tid; ii < brows; ii += nt)
+                    W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
+                if (tid == 0) { s_ext = c; s_wcol[0] = c; }
+                __syncthreads();
+            } else if (c != r) {
+                for (int ii = tid; ii < brows; ii += nt) {
+                    uint32_t x = W[ii * PIV_LDW + r];
+                    W[ii * PIV_LDW + r] = W[ii * PIV_LDW + c];
+                    W[ii * PIV_LDW + c] = x;
+                }
+                if (tid == 0) { int x = s_wcol[r]; s_wcol[r] = s_wcol[c]; s_wcol[c] = x; }
+                __syncthreads();
             }
-            // No pivot yet in this slab: row i of A is still the unreduced,
-            // unpermuted input, so its first nonzero beyond the window is read directly.
-            if (tid == 0) s_c = INT_MAX;
-            __syncthreads();
-            const uint32_t *row = A + (a + i) * lda + col0;
-            for (int64_t q = wne + tid; q < w; q += nt)
-                if (row[q]) { atomicMin(&s_c, (int)q); break; }
-            __syncthreads();
-            c = s_c;
-            __syncthreads();
-            if (c == INT_MAX) continue;        // zero row
-            for (int ii = tid; ii < brows; ii += nt)
-                W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
-            if (tid == 0) { s_ext = c; s_wcol[0] = c; }
-            __syncthreads();
-        } else if (c != r) {
-            for (int ii = tid; ii < brows; ii += nt) {
-                uint32_t x = W[ii * PIV_LDW + r];
-                W[ii * PIV_LDW + r] = W[ii * PIV_LDW + c];
-                W[ii * PIV_LDW + c] = x;
+            const uint32_t f = W[i * PIV_LDW + r];
+            if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
+            // panel rows below i: window positions (r, wne) and row-operation columns [0, pend);
+            // two warps per row, lanes along the columns
+            const int nrk = pend - 1 - i;
+            if (nrk > 0) {
+                const int nwc = wne - r - 1, ncol = nwc + pend;
+                const uint32_t *prow = W + i * PIV_LDW + r + 1, *perow = E + i * PIV_LDE;
+                for (int item = warp; item < 2 * nrk; item += nw) {
+                    const int k = i + 1 + (item >> 1);
+                    uint32_t *wk = W + k * PIV_LDW, *ek = E + k * PIV_LDE;
+                    const uint32_t mk = wk[r];
+                    uint32_t *wq = wk + r + 1;
+                    for (int q = (item & 1) * 32 + lane; q < ncol; q += 64) {
+                        if (q < nwc) wq[q] = ff<MONT>(f, wq[q], mk, prow[q], M);
+                        else ek[q - nwc] = ff<MONT>(f, ek[q - nwc], mk, perow[q - nwc], M);
+                    }
+                }
             }
-            if (tid == 0) { int x = s_wcol[r]; s_wcol[r] = s_wcol[c]; s_wcol[c] = x; }
             __syncthreads();
+            Sprod = scale_mul<MONT>(Sprod, f, M);
+            ++r;
         }
-        const uint32_t f = W[i * PIV_LDW + r];
-        if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
-        // rows below, window positions (r, wne): lanes take rows i+1+lane and
-        // i+33+lane (their multipliers in registers), warps take columns; the
-        // pivot-row entry of a column is one broadcast read
+        const int bp = r - r0;
+        if (bp == 0 || pend >= lim) continue;
+        // Rows [pend, lim) take the panel's bp pivots at once. With g_t the
+        // scale of step t (the update is z <- g_t z - R^{-1} m_t y_t), the bp
+        // sequential updates unroll to
+        //   z = (prod_t g_t) x - sum_t (R^{-1} prod_{t' > t} g_t') m_t y_t,
+        // where m_t is the row's entry at pivot position r0 + t just before step t.
         {
-            const uint32_t *prow = W + i * PIV_LDW;
-            const int ra = i + 1 + lane, rb = i + 33 + lane;
-            const bool va = ra < brows, vb = rb < brows;
-            uint32_t *wa = W + (va ? ra : 0) * PIV_LDW, *wb = W + (vb ? rb : 0) * PIV_LDW;
-            const uint32_t ma = va ? wa[r] : 0u, mb = vb ? wb[r] : 0u;
-            const int nw = nt >> 5;
-            if (i + 1 < brows) {
-                int q = r + 1 + warp;
-                for (; q + nw < wne; q += 2 * nw) {
-                    const uint32_t y0 = prow[q], y1 = prow[q + nw];
-                    uint32_t a0 = 0u, a1 = 0u, b0 = 0u, b1 = 0u;
-                    if (va) { a0 = wa[q]; a1 = wa[q + nw]; }
-                    if (vb) { b0 = wb[q]; b1 = wb[q + nw]; }
-                    if (va) { wa[q] = ff<MONT>(f, a0, ma, y0, M); wa[q + nw] = ff<MONT>(f, a1, ma, y1, M); }
-                    if (vb) { wb[q] = ff<MONT>(f, b0, mb, y0, M); wb[q + nw] = ff<MONT>(f, b1, mb, y1, M); }
+            // every warp forms h_t = R^{-1} prod_{t' > t} g_t' and A0 = prod_t g_t by a suffix scan
+            uint32_t g = one;
+            if (lane < bp) g = MONT ? redc((uint64_t)s_f[r0 + lane], M) : s_f[r0 + lane];
+            uint32_t suf = g;                                   // inclusive suffix product
+#pragma unroll
+            for (int o = 1; o < PIV_PB; o <<= 1) {
+                const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
+                if (lane + o < bp) suf = mulm(suf, u, M);
+            }
+            uint32_t h = __shfl_down_sync(0xffffffffu, suf, 1);
+            if (lane + 1 >= bp) h = one;
+            h = mulm(h, rinv, M);
+            const uint32_t A0 = __shfl_sync(0xffffffffu, suf, 0);
+            uint32_t hv[PIV_PB];
+#pragma unroll
+            for (int t = 0; t < PIV_PB; ++t) hv[t] = __shfl_sync(0xffffffffu, h, t);
+            // (b) one thread per row: the multipliers m_t by the recurrence restricted to the
+            // panel's pivot positions, stored where the unblocked elimination leaves them
+            const int k = pend + tid;
+            if (k < lim) {
+                uint32_t v[PIV_PB];
+#pragma unroll
+                for (int s2 = 0; s2 < PIV_PB; ++s2) v[s2] = (s2 < bp) ? W[k * PIV_LDW + r0 + s2] : 0u;
+#pragma unroll
+                for (int t = 0; t < PIV_PB; ++t) {
+                    if (t < bp) {
+                        const uint32_t m = v[t];
+                        W[k * PIV_LDW + r0 + t] = m;
+                        const uint32_t at = mulm(m, hv[t], M);
+                        s_coef[k][t] = at ? M.p - at : 0u;
+                        const uint32_t ft = s_f[r0 + t];
+                        const uint32_t *yt = W + s_prof[r0 + t] * PIV_LDW + r0;
+#pragma unroll
+                        for (int s2 = t + 1; s2 < PIV_PB; ++s2)
+                            if (s2 < bp) v[s2] = ff<MONT>(ft, v[s2], m, yt[s2], M);
+                    }
                 }
-                if (q < wne) {
-                    const uint32_t y0 = prow[q];
-                    if (va) wa[q] = ff<MONT>(f, wa[q], ma, y0, M);
-                    if (vb) wb[q] = ff<MONT>(f, wb[q], mb, y0, M);
+                // the row's own column of E only picks up the scale
+                E[k * PIV_LDE + k] = mulm(E[k * PIV_LDE + k], A0, M);
+            }
+            __syncthreads();
+            // (c) window positions [r, wne) and E columns [0, pend): lanes take rows
+            // pend + lane and pend + 32 + lane (their coefficients in registers), warps take columns
+            const int ka = pend + lane, kb = pend + 32 + lane;
+            const bool va = ka < lim, vb = kb < lim;
+            uint32_t ca[PIV_PB], cb[PIV_PB];
+            int pr[PIV_PB];
+#pragma unroll
+            for (int t = 0; t < PIV_PB; ++t) {
+                ca[t] = (va && t < bp) ? s_coef[ka][t] : 0u;
+                cb[t] = (vb && t < bp) ? s_coef[kb][t] : 0u;
+                pr[t] = (t < bp) ? s_prof[r0 + t] : 0;
+            }
+            const int nwc = wne - r, ncol = nwc + pend;
+            for (int q = warp; q < ncol; q += nw) {
+                const bool inw = q < nwc;
+                const int col = inw ? r + q : q - nwc;
+                uint32_t *xa = inw ? W + ka * PIV_LDW + col : E + ka * PIV_LDE + col;
+                uint32_t *xb = inw ? W + kb * PIV_LDW + col : E + kb * PIV_LDE + col;
+                uint64_t sa = va ? (uint64_t)A0 * *xa : 0ull, sb = vb ? (uint64_t)A0 * *xb : 0ull;
+                Acc aa = {0ull, 0u}, ab = {0ull, 0u};
+#pragma unroll
+                for (int t = 0; t < PIV_PB; ++t) {
+                    if (t < bp) {
+                        const uint32_t y = inw ? W[pr[t] * PIV_LDW + col] : E[pr[t] * PIV_LDE + col];
+                        if (WIDE) {
+                            acc_add(aa, (uint64_t)ca[t] * y);
+                            acc_add(ab, (uint64_t)cb[t] * y);
+                        } else {
+                            sa += (uint64_t)ca[t] * y;
+                            sb += (uint64_t)cb[t] * y;
+                        }
+                    }
+                }
+                if (WIDE) {
+                    acc_add(aa, sa);
+                    acc_add(ab, sb);
+                    if (va) *xa = acc_red(aa, M);
+                    if (vb) *xb = acc_red(ab, M);
+                } else {
+                    if (va) *xa = red64(sa, M);
+                    if (vb) *xb = red64(sb, M);
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        Sprod = scale_mul<MONT>(Sprod, f, M);
-        ++r;
     }
     const int rs = r;
 
@@ -205,62 +316,23 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     }
     __syncthreads();
 
-    // C values of the resolved rows: W[i][t] carries the scale S_t of step t;
-    // the pivot itself is f_t / S_t, so its inverse is S_t / f_t
-    for (int idx = tid; idx < stop * rs; idx += nt) {
-        int i = idx / rs, t = idx - i * rs;
-        uint32_t v = (i >= s_prof[t]) ? mulm(W[i * PIV_LDW + t], s_Sinv[t], M) : 0u;
-        S->Cn[i][t] = v;
-    }
-    __syncthreads();
-    // L^{-1} for the finish kernel, L[t][u] = C[prof t][u] (lower triangular,
-    // pivots on the diagonal), by merging inverted diagonal blocks:
-    // inv([L11 0; L21 L22]) = [inv(L11) 0; -inv(L22) L21 inv(L11), inv(L22)].
-    // The window W is free now; it holds L (cols 0..63), Linv (64..127) and a temporary.
+    // C values of the resolved rows: W[i][t] carries the scale S_t of step t.
+    // L^{-1} for the finish kernel: pivot row t of the eliminated slab is
+    // (E X)_t = f_t U_t, so U = diag(1/f) E_pp X over the pivot rows, i.e.
+    // L^{-1}[t][u] = E[prof t][prof u] / f_t (zero for u > t).
     {
-        uint32_t *sL = W;                                  // rs x rs, row stride PIV_LDW
-        uint32_t *sI = W + CUP_BMAX;                       // Linv, same rows, columns offset by 64
-        uint32_t *sT = W + (size_t)CUP_BMAX * PIV_LDW;     // temporary, only if brows > ... (see launcher)
-        for (int idx = tid; idx < rs * rs; idx += nt) {
-            const int t = idx / rs, u = idx - t * rs;
-            const uint32_t c = (u <= t) ? mulm(W[s_prof[t] * PIV_LDW + u], s_Sinv[u], M) : 0u;
-            sT[t * CUP_BMAX + u] = c;
+        const int t = tid & (CUP_BMAX - 1);
+        if (t < rs) {
+            const int pt = s_prof[t];
+            const uint32_t sinv = s_Sinv[t];
+            for (int i = tid >> 6; i < stop; i += nt >> 6)
+                S->Cn[i][t] = (i >= pt) ? mulm(W[i * PIV_LDW + t], sinv, M) : 0u;
         }
-        __syncthreads();
-        for (int idx = tid; idx < rs * rs; idx += nt) {
-            const int t = idx / rs, u = idx - t * rs;
-            sL[t * PIV_LDW + u] = sT[t * CUP_BMAX + u];
-            sI[t * PIV_LDW + u] = (u == t) ? mulm(s_Sfwd[t], s_finv[t], M) : 0u;
-        }
-        __syncthreads();
-        for (int sz = 1; sz < rs; sz *= 2) {
-            // T = L21 inv(L11) for every block pair at this level
-            for (int idx = tid; idx < rs * sz; idx += nt) {
-                const int t = idx / sz, uu = idx - t * sz;          // row t, column b0 + uu
-                const int b0 = (t / (2 * sz)) * (2 * sz);
-                if (t < b0 + sz) continue;                          // rows of the top block
-                const int u = b0 + uu;
-                Acc acc = {0ull, 0u};
-                for (int v = u; v < b0 + sz; ++v) acc_add(acc, (uint64_t)sL[t * PIV_LDW + v] * sI[v * PIV_LDW + u]);
-                sT[t * CUP_BMAX + u] = acc_red(acc, M);
-            }
-            __syncthreads();
-            // X21 = -inv(L22) T
-            for (int idx = tid; idx < rs * sz; idx += nt) {
-                const int t = idx / sz, uu = idx - t * sz;
-                const int b0 = (t / (2 * sz)) * (2 * sz);
-                if (t < b0 + sz) continue;
-                const int u = b0 + uu;
-                Acc acc = {0ull, 0u};
-                for (int v = b0 + sz; v <= t; ++v) acc_add(acc, (uint64_t)sI[t * PIV_LDW + v] * sT[v * CUP_BMAX + u]);
-                const uint32_t x = acc_red(acc, M);
-                sI[t * PIV_LDW + u] = x ? M.p - x : 0u;
-            }
-            __syncthreads();
-        }
-        for (int idx = tid; idx < rs * rs; idx += nt) {
-            const int t = idx / rs, u = idx - t * rs;
-            S->Linv[t][u] = sI[t * PIV_LDW + u];
+        const int u = tid & (CUP_BMAX - 1);
+        if (u < rs) {
+            const int pu = s_prof[u];
+            for (int t2 = tid >> 6; t2 < rs; t2 += nt >> 6)
+                S->Linv[t2][u] = mulm(E[s_prof[t2] * PIV_LDE + pu], s_finv[t2], M);
         }
     }
     for (int t = tid; t < rs; t += nt) S->pinv[t] = mulm(s_Sfwd[t], s_finv[t], M);
@@ -707,23 +779,33 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
                                int64_t *rank_next, cudaStream_t st)
 {
     static bool attr = false;
-    // window rows, then a CUP_BMAX^2 temporary used when inverting L
-    const size_t smem = ((size_t)CUP_BMAX * PIV_LDW + (size_t)CUP_BMAX * CUP_BMAX) * sizeof(uint32_t);
+    // window rows, then the row-operation matrix
+    const size_t smem = ((size_t)CUP_BMAX * PIV_LDW + (size_t)CUP_BMAX * PIV_LDE) * sizeof(uint32_t);
     (void)brows;
     if (!attr) {
         const int mx = (int)smem;
-        cudaError_t e = cudaFuncSetAttribute(k_slab_pivots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaError_t e = cudaFuncSetAttribute(k_slab_pivots<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_slab_pivots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            e = cudaFuncSetAttribute(k_slab_pivots<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_slab_pivots<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (M.p & 1u)
-        k_slab_pivots<true><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S, ipiv, prof,
-                                                            rank_next);
-    else
-        k_slab_pivots<false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S, ipiv, prof,
-                                                             rank_next);
+    // the block update sums PIV_PB + 1 products below p^2 in 64 bits when that cannot wrap
+    const uint64_t pm1 = M.p - 1u;
+    const bool wide = pm1 * pm1 > ~0ull / (uint64_t)(PIV_PB + 1);
+    if (M.p & 1u) {
+        if (wide)
+            k_slab_pivots<true, true><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S,
+                                                                     ipiv, prof, rank_next);
+        else
+            k_slab_pivots<true, false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S,
+                                                                      ipiv, prof, rank_next);
+    } else {
+        k_slab_pivots<false, false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S,
+                                                                   ipiv, prof, rank_next);
+    }
     return cudaGetLastError();
 }
 

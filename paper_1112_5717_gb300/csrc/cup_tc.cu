@@ -153,6 +153,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Montgomery step without the final subtraction: for x < 2^61, (x + m p) / R < 2^29 + p.
+__device__ __forceinline__ uint32_t redc_raw(uint64_t x, const ModP &M)
+{
+    const uint32_t m = (uint32_t)x * M.pneg;
+    return (uint32_t)((x + (uint64_t)m * M.p) >> 32);
+}
+
+// Barrier over the epilogue warps only (named barrier 1), OR-reducing a flag.
+__device__ __forceinline__ int epi_bar_or(int pred)
+{
+    int r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
+                 "selp.s32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"(pred), "n"(32 * NEPI)
+                 : "memory");
+    return r;
+}
+
 template <int L>
 struct Cfg {
     static constexpr int NACC = 2 * L - 1;
@@ -276,8 +295,13 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // ---------------- epilogue warps ----------------
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
         const int hcol = (warp - 2) >> 2;                 // which half of the BN columns
-        const int row = m0 + 32 * q + lane;
+        const int trow = 32 * q + lane;                   // row of the tile
         constexpr int CPW = CF::COLS_PER_WARP;
+        // Odd p with L <= 3: the recombined chunk value v < 2^60 is reduced by one
+        // Montgomery step (to v R^{-1}, below 2^32) and a 32-bit Barrett step; the
+        // running sum then carries R^{-1}, removed once at the end.
+        const bool mont = (L <= 3) && (Mp.p & 1u);
+        const uint32_t mu32 = (uint32_t)(Mp.mu >> 32);    // floor(2^32 / p) for odd p
         uint32_t run[CPW];
 #pragma unroll
         for (int e = 0; e < CPW; ++e) run[e] = 0u;
@@ -300,7 +324,14 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         int64_t v = 0;
 #pragma unroll
                         for (int s = NACC - 1; s >= 0; --s) v = v * 256 + (int64_t)__float2int_rn(d[s][e]);
-                        r = red64((uint64_t)(v + (int64_t)off), Mp);
+                        const uint64_t x = (uint64_t)(v + (int64_t)off);
+                        if (mont) {
+                            uint32_t t = redc_raw(x, Mp);                  // < 2^28 + p
+                            t -= __umulhi(t, mu32) * Mp.p;                 // < 2p
+                            r = t >= Mp.p ? t - Mp.p : t;
+                        } else {
+                            r = red64(x, Mp);
+                        }
                     } else {
                         int64_t lo = 0, hi = 0;
 #pragma unroll
@@ -318,12 +349,43 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar));
         }
-        if (ok && row < M) {
-            uint32_t *crow = C + (int64_t)row * ldc;
+        // Every MMA has completed (the last accumulator barrier), so the operand
+        // stages are free: the tile goes through shared memory and C is read and
+        // written row by row with the lanes along the columns.
+        constexpr int LDT = BN + 1;
+        uint32_t *tile = (uint32_t *)smem;
+        if (ok) {
 #pragma unroll
             for (int e = 0; e < CPW; ++e) {
-                const int gc = n0 + hcol * CPW + e;
-                if (gc < N) crow[gc] = add ? addm(crow[gc], run[e], Mp) : subm(crow[gc], run[e], Mp);
+                uint32_t v = run[e];
+                if (mont) v = redc((uint64_t)v * Mp.r2, Mp);      // v R
+                tile[trow * LDT + hcol * CPW + e] = v;
+            }
+        }
+        const int failed = epi_bar_or(ok ? 0 : 1);
+        if (!failed) {
+            // C is updated in batches of 32 elements per thread, each batch loaded
+            // completely before it is written back (one global round trip per batch)
+            constexpr int PER = BM * BN / (32 * NEPI), BATCH = 32;
+            const int et = threadIdx.x - 64;                  // 0 .. 32 NEPI - 1
+#pragma unroll
+            for (int b0 = 0; b0 < PER; b0 += BATCH) {
+                uint32_t cv[BATCH];
+#pragma unroll
+                for (int i = 0; i < BATCH; ++i) {
+                    const int e = et + 32 * NEPI * (b0 + i);
+                    const int rr = e / BN, cc = e % BN;
+                    cv[i] = (m0 + rr < M && n0 + cc < N) ? C[(int64_t)(m0 + rr) * ldc + n0 + cc] : 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < BATCH; ++i) {
+                    const int e = et + 32 * NEPI * (b0 + i);
+                    const int rr = e / BN, cc = e % BN;
+                    if (m0 + rr < M && n0 + cc < N) {
+                        const uint32_t v = tile[rr * LDT + cc];
+                        C[(int64_t)(m0 + rr) * ldc + n0 + cc] = add ? addm(cv[i], v, Mp) : subm(cv[i], v, Mp);
+                    }
+                }
             }
         }
     }
