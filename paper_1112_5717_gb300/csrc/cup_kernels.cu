@@ -45,6 +45,7 @@
 #ifndef PIV_PB
 #define PIV_PB 8                    // panel rows of the blocked window elimination
 #endif
+#define PIV_PW 8                    // warps that eliminate a panel
 
 // One fraction-free update f x - m y, scaled by R^{-1} in the Montgomery
 // variant (odd p): the common factor only changes the tracked row scales.
@@ -79,6 +80,18 @@ __device__ __forceinline__ int window_search(const uint32_t *row, int r, int wne
     return -1;
 }
 
+// Barrier over the warps that eliminate a panel (named barrier 1).
+__device__ __forceinline__ void panel_bar()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * PIV_PW) : "memory");
+}
+
+// Montgomery reduction of T < p R to [0, p) (odd p).
+__device__ __forceinline__ uint32_t redc_once(uint64_t T, const ModP &M)
+{
+    return redc(T, M);
+}
+
 template <bool MONT, bool WIDE>
 __global__ void __launch_bounds__(PIV_THREADS)
 k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const Dyn col0d,
@@ -102,8 +115,9 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX], s_spec[CUP_BMAX];
     __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_muinv[CUP_BMAX], s_Sinv[CUP_BMAX],
         s_Sfwd[CUP_BMAX];
-    __shared__ uint32_t s_coef[CUP_BMAX][PIV_PB + 1];   // -a_kt of the block update, per row below a panel
+    __shared__ __align__(16) uint32_t s_coef[CUP_BMAX][PIV_PB];   // -a_kt of the block update, per row below a panel
     __shared__ int s_c, s_ext;
+    __shared__ int s_state[2][6];              // after each panel: rank, stop, spec count, done, rows to update, swaps
     __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
 
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -126,163 +140,236 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     if (tid == 0) s_ext = -1;
     __syncthreads();
 
-    int r = 0, stop = brows, nspec = 0;
+    // Leading rows while the slab has no pivot (whole CTA): a row whose window
+    // is zero is either a zero row or has its first nonzero beyond the window,
+    // whose column then moves to position 0 (no elimination has happened yet,
+    // so the rows are still the unreduced input).
+    int p0 = 0;
+    for (; p0 < brows; ++p0) {
+        int c = window_search(W + p0 * PIV_LDW, 0, wne, lane);
+        if (c >= 0) break;
+        if ((int64_t)wne == w) continue;                   // zero row
+        if (tid == 0) s_c = INT_MAX;
+        __syncthreads();
+        const uint32_t *row = A + (a + p0) * lda + col0;
+        for (int64_t q = wne + tid; q < w; q += nt)
+            if (row[q]) { atomicMin(&s_c, (int)q); break; }
+        __syncthreads();
+        c = s_c;
+        __syncthreads();
+        if (c == INT_MAX) continue;                        // zero row
+        for (int ii = tid; ii < brows; ii += nt) W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
+        if (tid == 0) { s_ext = c; s_wcol[0] = c; }
+        __syncthreads();
+        break;
+    }
+    const int ext0 = s_ext;
+
+    int r = 0, stop = brows, nspec = 0, pc = 0;
     bool done = false;
-    uint32_t Sprod = one;                      // product of the row scales applied so far
-    for (int p0 = 0; p0 < brows && !done; p0 += PIV_PB) {
-        // Panel of rows [p0, pend): the rows are taken one by one as in the
-        // unblocked elimination, but each step only updates the panel's rows.
+    uint32_t Sprod = one;                      // product of the row scales applied so far (warp 0)
+    for (; p0 < brows && !done; p0 += PIV_PB, ++pc) {
         const int pend = p0 + PIV_PB < brows ? p0 + PIV_PB : brows;
         const int r0 = r;
-        int lim = brows;                       // rows that still need this panel's pivots
-        for (int i = p0; i < pend; ++i) {
-            if ((int64_t)r >= w) { done = true; break; }   // every column is a pivot: later rows are dependent
-            int c = window_search(W + i * PIV_LDW, r, wne, lane);
-            if (c < 0) {
-                if ((int64_t)wne == w) continue;   // whole residual known and zero
-                if (r != 0) {
+        if (warp < PIV_PW) {
+            // Panel of rows [p0, pend), eliminated by the first PIV_PW warps (named
+            // barrier 1): the rows are taken one by one as in the unblocked
+            // elimination, each step updating only the panel's rows. Warp w owns
+            // the 32-column chunk w of (window positions > r, then E columns [0, pend)).
+            int lim = brows;                   // rows that still need this panel's pivots
+            bool swapped = false;
+            for (int i = p0; i < pend; ++i) {
+                if ((int64_t)r >= w) { done = true; break; }   // every column is a pivot: later rows are dependent
+                const int c = window_search(W + i * PIV_LDW, r, wne, lane);
+                if (c < 0) {
+                    // r > 0 here: the first row of the first panel holds a window nonzero
+                    if ((int64_t)wne == w) continue;   // whole residual known and zero
                     if (!speculate) { stop = i; lim = i; done = true; break; }
                     if (tid == 0) s_spec[nspec] = i;   // verified by the finish kernel
                     ++nspec;
                     continue;
                 }
-                // No pivot yet in this slab: row i of A is still the unreduced,
-                // unpermuted input, so its first nonzero beyond the window is read directly.
-                if (tid == 0) s_c = INT_MAX;
-                __syncthreads();
-                const uint32_t *row = A + (a + i) * lda + col0;
-                for (int64_t q = wne + tid; q < w; q += nt)
-                    if (row[q]) { atomicMin(&s_c, (int)q); break; }
-                __syncthreads();
-                c = s_c;
-                __syncthreads();
-                if (c == INT_MAX) continue;        // zero row
-                for (int ii = tid; ii < brows; ii += nt)
-                    W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
-                if (tid == 0) { s_ext = c; s_wcol[0] = c; }
-                __syncthreads();
-            } else if (c != r) {
-                for (int ii = tid; ii < brows; ii += nt) {
-                    uint32_t x = W[ii * PIV_LDW + r];
-                    W[ii * PIV_LDW + r] = W[ii * PIV_LDW + c];
-                    W[ii * PIV_LDW + c] = x;
-                }
-                if (tid == 0) { int x = s_wcol[r]; s_wcol[r] = s_wcol[c]; s_wcol[c] = x; }
-                __syncthreads();
-            }
-            const uint32_t f = W[i * PIV_LDW + r];
-            if (tid == 0) { s_pos[r] = c; s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod; }
-            // panel rows below i: window positions (r, wne) and row-operation columns [0, pend);
-            // two warps per row, lanes along the columns
-            const int nrk = pend - 1 - i;
-            if (nrk > 0) {
-                const int nwc = wne - r - 1, ncol = nwc + pend;
-                const uint32_t *prow = W + i * PIV_LDW + r + 1, *perow = E + i * PIV_LDE;
-                for (int item = warp; item < 2 * nrk; item += nw) {
-                    const int k = i + 1 + (item >> 1);
-                    uint32_t *wk = W + k * PIV_LDW, *ek = E + k * PIV_LDE;
-                    const uint32_t mk = wk[r];
-                    uint32_t *wq = wk + r + 1;
-                    for (int q = (item & 1) * 32 + lane; q < ncol; q += 64) {
-                        if (q < nwc) wq[q] = ff<MONT>(f, wq[q], mk, prow[q], M);
-                        else ek[q - nwc] = ff<MONT>(f, ek[q - nwc], mk, perow[q - nwc], M);
+                if (c != r) {
+                    swapped = true;
+                    // transposition of positions r and c in the panel's rows (rows below
+                    // take it with the block update; rows above never read these positions),
+                    // once every warp has searched row i
+                    panel_bar();
+                    for (int ii = p0 + tid; ii < pend; ii += 32 * PIV_PW) {
+                        const uint32_t x = W[ii * PIV_LDW + r];
+                        W[ii * PIV_LDW + r] = W[ii * PIV_LDW + c];
+                        W[ii * PIV_LDW + c] = x;
                     }
+                    if (tid == 0) { const int x = s_wcol[r]; s_wcol[r] = s_wcol[c]; s_wcol[c] = x; }
+                    panel_bar();
                 }
+                const uint32_t f = W[i * PIV_LDW + r];
+                if (tid == 0) {
+                    s_pos[r] = (r == 0 && ext0 >= 0) ? ext0 : c;
+                    s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod;
+                }
+                const int nwc = wne - r - 1;
+                const int ci = 32 * warp + lane;
+                if (ci < nwc + pend) {
+                    // every operand of the (at most PIV_PB - 1) rows is read before any result is stored
+                    const bool inw = ci < nwc;
+                    const uint32_t y = inw ? W[i * PIV_LDW + r + 1 + ci] : E[i * PIV_LDE + ci - nwc];
+                    uint32_t *xk = inw ? W + (i + 1) * PIV_LDW + r + 1 + ci : E + (i + 1) * PIV_LDE + ci - nwc;
+                    const int xs = inw ? PIV_LDW : PIV_LDE;
+                    const int nk = pend - 1 - i;
+                    uint32_t mk[PIV_PB - 1], xv[PIV_PB - 1];
+#pragma unroll
+                    for (int j = 0; j < PIV_PB - 1; ++j)
+                        if (j < nk) { mk[j] = W[(i + 1 + j) * PIV_LDW + r]; xv[j] = xk[j * xs]; }
+#pragma unroll
+                    for (int j = 0; j < PIV_PB - 1; ++j)
+                        if (j < nk) xk[j * xs] = ff<MONT>(f, xv[j], mk[j], y, M);
+                }
+                panel_bar();
+                Sprod = scale_mul<MONT>(Sprod, f, M);
+                ++r;
             }
-            __syncthreads();
-            Sprod = scale_mul<MONT>(Sprod, f, M);
-            ++r;
+            if (tid == 0) {
+                int *st = s_state[pc & 1];
+                st[0] = r; st[1] = stop; st[2] = nspec; st[3] = done ? 1 : 0; st[4] = lim;
+                st[5] = swapped ? 1 : 0;
+            }
         }
+        __syncthreads();
+        const int lim = s_state[pc & 1][4];
+        r = s_state[pc & 1][0]; stop = s_state[pc & 1][1]; nspec = s_state[pc & 1][2];
+        done = s_state[pc & 1][3] != 0;
+        const bool pswap = s_state[pc & 1][5] != 0;
         const int bp = r - r0;
         if (bp == 0 || pend >= lim) continue;
-        // Rows [pend, lim) take the panel's bp pivots at once. With g_t the
-        // scale of step t (the update is z <- g_t z - R^{-1} m_t y_t), the bp
-        // sequential updates unroll to
+        // Rows [pend, lim) take the panel's transpositions, then its bp pivots
+        // at once. With g_t the scale of step t (the update is
+        // z <- g_t z - R^{-1} m_t y_t), the bp sequential updates unroll to
         //   z = (prod_t g_t) x - sum_t (R^{-1} prod_{t' > t} g_t') m_t y_t,
         // where m_t is the row's entry at pivot position r0 + t just before step t.
         {
-            // every warp forms h_t = R^{-1} prod_{t' > t} g_t' and A0 = prod_t g_t by a suffix scan
-            uint32_t g = one;
-            if (lane < bp) g = MONT ? redc((uint64_t)s_f[r0 + lane], M) : s_f[r0 + lane];
-            uint32_t suf = g;                                   // inclusive suffix product
+            // Every warp forms h_t = R^{-1} prod_{t' > t} g_t' and A0 = prod_t g_t by a
+            // suffix scan. For odd p it runs on Montgomery representations, where g_t
+            // is represented by f_t itself (g_t R = f_t): the exclusive suffix product
+            // is then h_t R^2 and the inclusive one A0 R, the forms the update uses.
+            uint32_t h, A0, A0f;
+            if (MONT) {
+                uint32_t suf = (lane < bp) ? s_f[r0 + lane] : redc((uint64_t)M.r2, M);   // R mod p: one
 #pragma unroll
-            for (int o = 1; o < PIV_PB; o <<= 1) {
-                const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
-                if (lane + o < bp) suf = mulm(suf, u, M);
-            }
-            uint32_t h = __shfl_down_sync(0xffffffffu, suf, 1);
-            if (lane + 1 >= bp) h = one;
-            h = mulm(h, rinv, M);
-            const uint32_t A0 = __shfl_sync(0xffffffffu, suf, 0);
-            uint32_t hv[PIV_PB];
-#pragma unroll
-            for (int t = 0; t < PIV_PB; ++t) hv[t] = __shfl_sync(0xffffffffu, h, t);
-            // (b) one thread per row: the multipliers m_t by the recurrence restricted to the
-            // panel's pivot positions, stored where the unblocked elimination leaves them
-            const int k = pend + tid;
-            if (k < lim) {
-                uint32_t v[PIV_PB];
-#pragma unroll
-                for (int s2 = 0; s2 < PIV_PB; ++s2) v[s2] = (s2 < bp) ? W[k * PIV_LDW + r0 + s2] : 0u;
-#pragma unroll
-                for (int t = 0; t < PIV_PB; ++t) {
-                    if (t < bp) {
-                        const uint32_t m = v[t];
-                        W[k * PIV_LDW + r0 + t] = m;
-                        const uint32_t at = mulm(m, hv[t], M);
-                        s_coef[k][t] = at ? M.p - at : 0u;
-                        const uint32_t ft = s_f[r0 + t];
-                        const uint32_t *yt = W + s_prof[r0 + t] * PIV_LDW + r0;
-#pragma unroll
-                        for (int s2 = t + 1; s2 < PIV_PB; ++s2)
-                            if (s2 < bp) v[s2] = ff<MONT>(ft, v[s2], m, yt[s2], M);
-                    }
+                for (int o = 1; o < PIV_PB; o <<= 1) {
+                    const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
+                    if (lane + o < bp) suf = redc((uint64_t)suf * u, M);
                 }
-                // the row's own column of E only picks up the scale
-                E[k * PIV_LDE + k] = mulm(E[k * PIV_LDE + k], A0, M);
-            }
-            __syncthreads();
-            // (c) window positions [r, wne) and E columns [0, pend): lanes take rows
-            // pend + lane and pend + 32 + lane (their coefficients in registers), warps take columns
-            const int ka = pend + lane, kb = pend + 32 + lane;
-            const bool va = ka < lim, vb = kb < lim;
-            uint32_t ca[PIV_PB], cb[PIV_PB];
-            int pr[PIV_PB];
+                const uint32_t oneR = redc((uint64_t)M.r2, M);
+                uint32_t ex = __shfl_down_sync(0xffffffffu, suf, 1);
+                if (lane + 1 >= bp) ex = oneR;
+                const uint32_t incl0 = __shfl_sync(0xffffffffu, suf, 0);
+                A0f = redc((uint64_t)incl0, M);                  // A0
+                if (!WIDE) {
+                    h = ex;                                      // h_t R^2
+                    A0 = incl0;                                  // A0 R
+                } else {
+                    h = redc((uint64_t)redc((uint64_t)ex, M), M); // h_t
+                    A0 = A0f;
+                }
+            } else {
+                uint32_t suf = (lane < bp) ? s_f[r0 + lane] : one;
 #pragma unroll
-            for (int t = 0; t < PIV_PB; ++t) {
-                ca[t] = (va && t < bp) ? s_coef[ka][t] : 0u;
-                cb[t] = (vb && t < bp) ? s_coef[kb][t] : 0u;
-                pr[t] = (t < bp) ? s_prof[r0 + t] : 0;
+                for (int o = 1; o < PIV_PB; o <<= 1) {
+                    const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
+                    if (lane + o < bp) suf = mulm(suf, u, M);
+                }
+                h = __shfl_down_sync(0xffffffffu, suf, 1);
+                if (lane + 1 >= bp) h = one;
+                A0 = __shfl_sync(0xffffffffu, suf, 0);
+                A0f = A0;
             }
-            const int nwc = wne - r, ncol = nwc + pend;
-            for (int q = warp; q < ncol; q += nw) {
-                const bool inw = q < nwc;
-                const int col = inw ? r + q : q - nwc;
-                uint32_t *xa = inw ? W + ka * PIV_LDW + col : E + ka * PIV_LDE + col;
-                uint32_t *xb = inw ? W + kb * PIV_LDW + col : E + kb * PIV_LDE + col;
-                uint64_t sa = va ? (uint64_t)A0 * *xa : 0ull, sb = vb ? (uint64_t)A0 * *xb : 0ull;
-                Acc aa = {0ull, 0u}, ab = {0ull, 0u};
-#pragma unroll
-                for (int t = 0; t < PIV_PB; ++t) {
-                    if (t < bp) {
-                        const uint32_t y = inw ? W[pr[t] * PIV_LDW + col] : E[pr[t] * PIV_LDE + col];
-                        if (WIDE) {
-                            acc_add(aa, (uint64_t)ca[t] * y);
-                            acc_add(ab, (uint64_t)cb[t] * y);
-                        } else {
-                            sa += (uint64_t)ca[t] * y;
-                            sb += (uint64_t)cb[t] * y;
+            // (b) eight lanes per row (four rows per warp): the panel's transpositions, then
+            // the multipliers m_t by the recurrence restricted to the panel's pivot
+            // positions (lane s holds position r0 + s; step t broadcasts lane t's value),
+            // stored where the unblocked elimination leaves them, and the coefficients
+            // of the fused update (zero for t >= bp)
+            {
+                const int kr = 4 * warp + (lane >> 3), s = lane & 7;
+                const int k = pend + kr;
+                const bool vk = k < lim;
+                uint32_t *wk = W + (vk ? k : pend) * PIV_LDW;
+                if (pswap && vk && s == 0) {
+                    for (int t = 0; t < bp; ++t) {
+                        const int ct = s_pos[r0 + t];
+                        if (ct != r0 + t && ct < wne) {
+                            const uint32_t x = wk[r0 + t];
+                            wk[r0 + t] = wk[ct];
+                            wk[ct] = x;
                         }
                     }
                 }
-                if (WIDE) {
-                    acc_add(aa, sa);
-                    acc_add(ab, sb);
-                    if (va) *xa = acc_red(aa, M);
-                    if (vb) *xb = acc_red(ab, M);
-                } else {
-                    if (va) *xa = red64(sa, M);
-                    if (vb) *xb = red64(sb, M);
+                __syncwarp();
+                const uint32_t hs = __shfl_sync(0xffffffffu, h, s);   // h_s, held by lane s
+                uint32_t v = (vk && s < bp) ? wk[r0 + s] : 0u;
+                uint32_t yv[PIV_PB - 1], fv[PIV_PB - 1];
+#pragma unroll
+                for (int t = 0; t < PIV_PB - 1; ++t) {
+                    const bool u = t < bp && s > t && s < bp;
+                    fv[t] = u ? s_f[r0 + t] : 0u;
+                    yv[t] = u ? W[s_prof[r0 + t] * PIV_LDW + r0 + s] : 0u;
+                }
+#pragma unroll
+                for (int t = 0; t < PIV_PB - 1; ++t) {
+                    const uint32_t m = __shfl_sync(0xffffffffu, v, (lane & ~7) | t);
+                    if (t < bp && s > t && s < bp) v = ff<MONT>(fv[t], v, m, yv[t], M);
+                }
+                if (vk) {
+                    uint32_t cf = 0u;
+                    if (s < bp) {
+                        wk[r0 + s] = v;
+                        const uint32_t at = (MONT && !WIDE) ? redc_once((uint64_t)v * hs, M) : mulm(v, hs, M);
+                        cf = at ? M.p - at : 0u;
+                    }
+                    s_coef[k][s] = cf;
+                    // the row's own column of E only picks up the scale
+                    if (s == 0) E[k * PIV_LDE + k] = mulm(E[k * PIV_LDE + k], A0f, M);
+                }
+            }
+            __syncthreads();
+            // (c) window positions [r, wne) and E columns [0, pend) of rows [pend, lim):
+            // a warp takes 32 columns (the panel's pivot-row entries in registers) and
+            // 8 rows (coefficients read as broadcast vectors)
+            {
+                int pr[PIV_PB];
+#pragma unroll
+                for (int t = 0; t < PIV_PB; ++t) pr[t] = s_prof[r0 + (t < bp ? t : 0)];
+                const int nwc = wne - r, ncol = nwc + pend;
+                const int nch = (ncol + 31) >> 5, nrg = (lim - pend + 7) >> 3;
+                for (int it = warp; it < nch * nrg; it += nw) {
+                    const int rg = it / nch, ch = it - rg * nch;
+                    const int ci = 32 * ch + lane;
+                    if (ci >= ncol) continue;
+                    const bool inw = ci < nwc;
+                    const int col = inw ? r + ci : ci - nwc;
+                    const uint32_t *ybase = inw ? W + col : E + col;
+                    const int ys = inw ? PIV_LDW : PIV_LDE;
+                    uint32_t y[PIV_PB];
+#pragma unroll
+                    for (int t = 0; t < PIV_PB; ++t) y[t] = ybase[pr[t] * ys];
+                    const int k0 = pend + 8 * rg, k1 = k0 + 8 < lim ? k0 + 8 : lim;
+                    uint32_t *xp = (inw ? W : E) + k0 * ys + col;
+                    for (int k = k0; k < k1; ++k, xp += ys) {
+                        const uint4 c0 = *(const uint4 *)&s_coef[k][0];
+                        const uint4 c1 = *(const uint4 *)&s_coef[k][4];
+                        const uint32_t cf[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                        if (WIDE) {
+                            Acc acc = {(uint64_t)A0 * *xp, 0u};
+#pragma unroll
+                            for (int t = 0; t < PIV_PB; ++t) acc_add(acc, (uint64_t)cf[t] * y[t]);
+                            *xp = acc_red(acc, M);
+                        } else {
+                            uint64_t sum = (uint64_t)A0 * *xp;
+#pragma unroll
+                            for (int t = 0; t < PIV_PB; ++t) sum += (uint64_t)cf[t] * y[t];
+                            *xp = MONT ? redc_once(sum, M) : red64(sum, M);
+                        }
+                    }
                 }
             }
             __syncthreads();
