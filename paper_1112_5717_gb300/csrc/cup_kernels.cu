@@ -15,6 +15,7 @@
 // path; the scale factors are products of the pivots and are divided out once
 // at the end with inversions computed in parallel.
 #include <climits>
+#include <cuda_bf16.h>
 #include "cup_internal.cuh"
 
 // ---------------------------------------------------------------------------
@@ -478,11 +479,43 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 // matrix) and C in the slab rows. Rows taken as dependent by a speculating
 // pivot kernel are checked here: their residual x - C u must vanish.
 // ---------------------------------------------------------------------------
-template <bool WIDE>
+// Centred base-256 digits of a residue: x = sum_l d_l 256^l (mod p), |d_l| <= 128,
+// exact in bf16.
+template <int L>
+__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, __nv_bfloat16 (&d)[L])
+{
+    int32_t v = (x > (p >> 1)) ? (int32_t)(x - p) : (int32_t)x;
+#pragma unroll
+    for (int l = 0; l < L - 1; ++l) {
+        const int32_t dl = ((v + 128) & 255) - 128;
+        d[l] = __int2bfloat16_rn(dl);
+        v = (v - dl) >> 8;
+    }
+    d[L - 1] = __int2bfloat16_rn(v);
+}
+
+// D += A B for one 16 x 8 tile: A 16 x 16 (row), B 16 x 8 (col), bf16 in, fp32 accumulate.
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+#define FIN_LD 72   // bf16 row stride of the digit planes (144 bytes: conflict-free fragment loads)
+
+// MODE 0 / 1: U = Linv X by 64-bit CUDA-core products (1: wide sums); MODE 2 + l:
+// by tensor-core bf16 products of l-limb digits (fp32 partial sums stay exact:
+// 64 * l * 2^14 < 2^24), recombined in 64 bits.
+template <int MODE>
 __global__ void __launch_bounds__(256)
 k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d, int64_t n, ModP M,
-              SlabScratch *__restrict__ S, int *__restrict__ err)
+              SlabScratch *__restrict__ S, int *__restrict__ err, uint64_t off)
 {
+    constexpr bool WIDE = MODE == 1;
+    constexpr int TCL = MODE >= 2 ? MODE - 1 : 0;
+    constexpr int TL = TCL > 0 ? TCL : 1;            // array extent for the digit code
     const int64_t col0 = col0d.eval();
     const int64_t w = n - col0;
     __shared__ uint32_t sL[CUP_BMAX][CUP_BMAX + 1];
@@ -522,13 +555,96 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
             if (t < rs && u < nq)
                 xv[k] = (slot >= 0) ? S->Dorig[slot][sProf[t]] : A[(a + sProf[t]) * lda + col0 + orig];
         }
+        if (TCL == 0) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            sL[t0 + 4 * k][u] = lv[k];
-            sX[t0 + 4 * k][u] = xv[k];
+            for (int k = 0; k < 16; ++k) {
+                sL[t0 + 4 * k][u] = lv[k];
+                sX[t0 + 4 * k][u] = xv[k];
+            }
+        } else {
+            // digit planes: Linv row-major (k = u contiguous), X transposed (n = u rows, k = t contiguous)
+            extern __shared__ __align__(16) uint8_t fdyn[];
+            __nv_bfloat16 *Ld = (__nv_bfloat16 *)fdyn;
+            __nv_bfloat16 *Xt = Ld + TL * CUP_BMAX * FIN_LD;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int t = t0 + 4 * k;
+                __nv_bfloat16 dl[TL], dx[TL];
+                limb_digits<TL>(lv[k], M.p, dl);
+                limb_digits<TL>(xv[k], M.p, dx);
+#pragma unroll
+                for (int l = 0; l < TCL; ++l) {
+                    Ld[(l * CUP_BMAX + t) * FIN_LD + u] = dl[l];
+                    Xt[(l * CUP_BMAX + u) * FIN_LD + t] = dx[l];
+                }
+            }
         }
     }
     __syncthreads();
+    if (TCL > 0) {
+        // U tile = Linv X on the tensor cores: warp (mt, nh) owns rows 16 mt .. + 15 and
+        // columns 32 nh .. + 31 (four 16 x 8 tiles); shift s = i + j collects the digit
+        // products A_i B_j
+        constexpr int NS = 2 * TL - 1;
+        extern __shared__ __align__(16) uint8_t fdyn[];
+        const __nv_bfloat16 *Ld = (const __nv_bfloat16 *)fdyn;
+        const __nv_bfloat16 *Xt = Ld + TL * CUP_BMAX * FIN_LD;
+        const int warp = tid >> 5, lane = tid & 31;
+        const int mt = warp & 3, nh = warp >> 2, g = lane >> 2, tq = lane & 3;
+        float acc[NS][4][4];
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[s2][j][e] = 0.f;
+        const int nks = (rs + 15) >> 4;
+        for (int ks = 0; ks < nks; ++ks) {
+            const int k0 = 16 * ks + 2 * tq;
+            uint32_t af[TL][4];
+#pragma unroll
+            for (int i = 0; i < TCL; ++i) {
+                const __nv_bfloat16 *ar = Ld + (i * CUP_BMAX + 16 * mt + g) * FIN_LD + k0;
+                af[i][0] = *(const uint32_t *)ar;
+                af[i][1] = *(const uint32_t *)(ar + 8 * FIN_LD);
+                af[i][2] = *(const uint32_t *)(ar + 8);
+                af[i][3] = *(const uint32_t *)(ar + 8 * FIN_LD + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+                for (int j = 0; j < TCL; ++j) {
+                    const __nv_bfloat16 *br = Xt + (j * CUP_BMAX + 32 * nh + 8 * nt + g) * FIN_LD + k0;
+                    const uint32_t b0 = *(const uint32_t *)br, b1 = *(const uint32_t *)(br + 8);
+#pragma unroll
+                    for (int i = 0; i < TCL; ++i) mma_16816(acc[i + j][nt], af[i], b0, b1);
+                }
+            }
+        }
+        __syncthreads();                                   // every digit read is done
+        const uint32_t mu32 = (uint32_t)(M.mu >> 32);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int t = 16 * mt + g + 8 * (e >> 1), qq = 32 * nh + 8 * nt + 2 * tq + (e & 1);
+                int64_t v = 0;
+#pragma unroll
+                for (int s2 = NS - 1; s2 >= 0; --s2) v = v * 256 + (int64_t)__float2int_rn(acc[s2][nt][e]);
+                const uint64_t x = (uint64_t)(v + (int64_t)off);
+                uint32_t rr;
+                if (M.p & 1u) {
+                    const uint32_t m = (uint32_t)x * M.pneg;
+                    uint32_t tt = (uint32_t)((x + (uint64_t)m * M.p) >> 32);   // x R^{-1} + (< p), below 2^32
+                    tt -= __umulhi(tt, mu32) * M.p;
+                    if (tt >= M.p) tt -= M.p;
+                    rr = redc((uint64_t)tt * M.r2, M);                       // times R
+                } else {
+                    rr = red64(x, M);
+                }
+                if (t < rs) sX[t][qq] = rr;
+            }
+    } else {
     // U tile = Linv X: each thread a 4 x 4 block (rows ty + 16 i, columns tx + 16 j)
     {
         const int tx = tid & 15, ty = tid >> 4;
@@ -570,6 +686,7 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
                 }
             }
     }
+    }
     __syncthreads();
     // rows taken as dependent: residual x_i - sum_t C[i][t] u_t must be zero at every position
     const int nspec = S->n_spec;
@@ -604,6 +721,7 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
     // rows: U rows col0 + t (t < rs), then slab rows a + i (i < stop) that are not U rows
     const int nrow = rs + stop;
     const int qq = tid & (CUP_QT - 1);
+#pragma unroll 4
     for (int k = tid >> 6; k < nrow; k += nt >> 6) {
         if (qq >= nq) continue;
         int64_t q = q0 + qq;
@@ -902,11 +1020,32 @@ cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, in
     const int64_t wmax = n - col0.lo;
     int64_t nb = (wmax + CUP_QT - 1) / CUP_QT;
     if (nb <= 0) return cudaSuccess;
-    // CUP_BMAX (p-1)^2 < 2^64 means a row of Minv times a column of X cannot wrap
-    // a row of Linv times a column of X sums CUP_BMAX products
+    const uint32_t p = M.p;
+    if (p < (1u << 24)) {
+        // tensor-core product of l-limb digits; the recombined value is below 2^55 in size
+        const int l = p < (1u << 8) ? 1 : p < (1u << 16) ? 2 : 3;
+        const uint64_t off = ((1ull << 55) / p + 1) * p;
+        const int smem = 2 * l * CUP_BMAX * FIN_LD * 2;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_slab_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 1 * CUP_BMAX * FIN_LD * 2);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_slab_finish<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 2 * CUP_BMAX * FIN_LD * 2);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_slab_finish<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 3 * CUP_BMAX * FIN_LD * 2);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        SlabScratch *Sm = const_cast<SlabScratch *>(S);
+        if (l == 1) k_slab_finish<2><<<(unsigned)nb, 256, smem, st>>>(A, lda, a, col0, n, M, Sm, err, off);
+        else if (l == 2) k_slab_finish<3><<<(unsigned)nb, 256, smem, st>>>(A, lda, a, col0, n, M, Sm, err, off);
+        else k_slab_finish<4><<<(unsigned)nb, 256, smem, st>>>(A, lda, a, col0, n, M, Sm, err, off);
+        return cudaGetLastError();
+    }
+    // a row of Linv times a column of X sums CUP_BMAX products: wide sums unless CUP_BMAX (p-1)^2 < 2^64
     const bool wide = (long double)CUP_BMAX * (M.p - 1) * (long double)(M.p - 1) >= 18446744073709551615.0L;
-    if (wide) k_slab_finish<true><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err);
-    else k_slab_finish<false><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err);
+    if (wide) k_slab_finish<1><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err, 0);
+    else k_slab_finish<0><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err, 0);
     return cudaGetLastError();
 }
 
