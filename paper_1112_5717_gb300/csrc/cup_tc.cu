@@ -151,6 +151,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Barrier over the epilogue warps only (named barrier 1).
+__device__ __forceinline__ void epi_bar()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Montgomery step without the final subtraction: for x < 2^61, (x + m p) / R < 2^29 + p.
@@ -160,17 +185,6 @@ __device__ __forceinline__ uint32_t redc_raw(uint64_t x, const ModP &M)
     return (uint32_t)((x + (uint64_t)m * M.p) >> 32);
 }
 
-// Barrier over the epilogue warps only (named barrier 1), OR-reducing a flag.
-__device__ __forceinline__ int epi_bar_or(int pred)
-{
-    int r;
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
-                 "selp.s32 %0, 1, 0, q;\n\t}"
-                 : "=r"(r)
-                 : "r"(pred), "n"(32 * NEPI)
-                 : "memory");
-    return r;
-}
 
 template <int L>
 struct Cfg {
@@ -180,7 +194,10 @@ struct Cfg {
     static constexpr int STAGE_B = BN * BK * 2;
     static constexpr int STAGE = L * (STAGE_A + STAGE_B);
     static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 8 ? (SMEM_BUDGET / STAGE) : 8;
-    static constexpr int SMEM = NSTAGE * STAGE + 1024;
+    static constexpr int CBUF = BM * BN * 4;                  // a C tile (prefetch when K is short)
+    static constexpr int SMEMUSE = (NSTAGE * STAGE > (NSTAGE - 1) * STAGE + CBUF) ? NSTAGE * STAGE
+                                                                                   : (NSTAGE - 1) * STAGE + CBUF;
+    static constexpr int SMEM = SMEMUSE + 1024;
     static constexpr int KCHUNK = (1024 / L) / BK * BK;      // L * kc * 2^14 <= 2^24
     static constexpr int COLS_PER_WARP = BN / 2;
 };
@@ -210,6 +227,9 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int nkb = Kp / BK;
     const int kb_chunk = CF::KCHUNK / BK;
     const int nchunk = (nkb + kb_chunk - 1) / kb_chunk;
+    // a short K uses fewer stages; the C tile is then prefetched into the spare space
+    const int nst = nkb < NSTAGE ? nkb : NSTAGE;
+    const bool pref = nkb < NSTAGE;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
@@ -237,8 +257,8 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (lane == 0) {
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % NSTAGE;
-                const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
+                const int s = kb % nst;
+                const uint32_t ph = (uint32_t)(kb / nst) & 1u;
                 if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, 1)) break;
                 const uint32_t fb = smem_u32(&full_bar[s]);
                 mbar_expect_tx(fb, CF::STAGE);
@@ -251,8 +271,8 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 ++issued;
             }
             // before leaving, let every issued copy land (bounded)
-            for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
-                mbar_wait(smem_u32(&full_bar[kb % NSTAGE]), (uint32_t)(kb / NSTAGE) & 1u, err, 2);
+            for (int kb = (issued > nst ? issued - nst : 0); kb < issued; ++kb)
+                mbar_wait(smem_u32(&full_bar[kb % nst]), (uint32_t)(kb / nst) & 1u, err, 2);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -266,8 +286,8 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 const int kb_first = kb;
                 const int kb_end = (kb + kb_chunk < nkb) ? kb + kb_chunk : nkb;
                 for (; kb < kb_end; ++kb) {
-                    const int s = kb % NSTAGE;
-                    const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
+                    const int s = kb % nst;
+                    const uint32_t ph = (uint32_t)(kb / nst) & 1u;
                     if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, 4)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t st = sbase + s * CF::STAGE;
@@ -293,32 +313,59 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else {
         // ---------------- epilogue warps ----------------
+        // (1) With a short K the C tile is copied asynchronously (coalesced) into
+        // the shared memory the unused stages leave, while the MMAs run.
+        // (2) Per chunk, warp w reads TMEM lane quarter w % 4 (one row per thread)
+        // and half of the columns, recombines the shift accumulators in 64 bits and
+        // reduces them; partial sums of earlier chunks wait in the TMEM columns
+        // after the accumulators. (3) The reduced tile goes through stage 0 (free
+        // once the last MMA has completed; XOR-swizzled rows keep both access
+        // patterns free of bank conflicts) back to the coalesced layout, and C is
+        // updated with the lanes along the columns.
+        const int et = threadIdx.x - 64;                  // 0 .. 32 NEPI - 1
+        constexpr int PER = BM * BN / (32 * NEPI);        // C entries per thread
+        uint32_t *cbuf = (uint32_t *)(smem + CF::SMEMUSE - CF::CBUF);
+        if (pref) {
+#pragma unroll 8
+            for (int i = 0; i < PER; ++i) {
+                const int e = et + 32 * NEPI * i, rr = e / BN, cc = e % BN;
+                if (m0 + rr < M && n0 + cc < N) cp_async4(cbuf + e, C + (int64_t)(m0 + rr) * ldc + n0 + cc);
+            }
+        }
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
-        const int hcol = (warp - 2) >> 2;                 // which half of the BN columns
-        const int trow = 32 * q + lane;                   // row of the tile
-        constexpr int CPW = CF::COLS_PER_WARP;
-        // Odd p with L <= 3: the recombined chunk value v < 2^60 is reduced by one
-        // Montgomery step (to v R^{-1}, below 2^32) and a 32-bit Barrett step; the
-        // running sum then carries R^{-1}, removed once at the end.
+        const int cg = (warp - 2) >> 2;                   // which half of the BN columns
+        constexpr int CPW = BN / 2;                       // columns per thread
+        constexpr int CW = 8;                             // columns per TMEM load
+        const uint32_t trow = (uint32_t)(32 * q) << 16;
+        const int srow = 32 * q + lane;                   // this thread's row of the tile
+        // Odd p with L <= 3: A's digits carry the factor R (the split stores A R mod p),
+        // so one Montgomery step of the recombined value v < 2^61 gives the product
+        // itself, below 2^29 + p, and a 32-bit Barrett step finishes the reduction.
         const bool mont = (L <= 3) && (Mp.p & 1u);
         const uint32_t mu32 = (uint32_t)(Mp.mu >> 32);    // floor(2^32 / p) for odd p
-        uint32_t run[CPW];
-#pragma unroll
-        for (int e = 0; e < CPW; ++e) run[e] = 0u;
+        uint32_t *tile = (uint32_t *)smem;
         bool ok = true;
         for (int c = 0; c < nchunk; ++c) {
             if (!mbar_wait(smem_u32(&accf_bar), (uint32_t)c & 1u, err, 5)) { ok = false; break; }
             tc_fence_after();
+            const bool last = c == nchunk - 1;
 #pragma unroll
-            for (int cb = 0; cb < CPW / 16; ++cb) {
-                const int col = hcol * CPW + cb * 16;
-                const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col;
-                float d[NACC][16];
+            for (int cb = 0; cb < CPW / CW; ++cb) {
+                const int col = cg * CPW + cb * CW;
+                const uint32_t tbase = tmem + trow + (uint32_t)col;
+                float d[NACC][CW];
 #pragma unroll
-                for (int s = 0; s < NACC; ++s) tmem_ld16(tbase + s * BN, d[s]);
+                for (int s = 0; s < NACC; ++s) tmem_ld8(tbase + s * BN, d[s]);
+                uint32_t run[CW];
+                if (c > 0) {
+                    float rf[CW];
+                    tmem_ld8(tbase + NACC * BN, rf);
+#pragma unroll
+                    for (int e = 0; e < CW; ++e) run[e] = __float_as_uint(rf[e]);
+                }
                 tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
+                for (int e = 0; e < CW; ++e) {
                     uint32_t r;
                     if (L <= 3) {
                         int64_t v = 0;
@@ -326,8 +373,8 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         for (int s = NACC - 1; s >= 0; --s) v = v * 256 + (int64_t)__float2int_rn(d[s][e]);
                         const uint64_t x = (uint64_t)(v + (int64_t)off);
                         if (mont) {
-                            uint32_t t = redc_raw(x, Mp);                  // < 2^28 + p
-                            t -= __umulhi(t, mu32) * Mp.p;                 // < 2p
+                            uint32_t t = redc_raw(x, Mp);
+                            t -= __umulhi(t, mu32) * Mp.p;
                             r = t >= Mp.p ? t - Mp.p : t;
                         } else {
                             r = red64(x, Mp);
@@ -342,47 +389,39 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         uint32_t rh = red64((uint64_t)(hi + (int64_t)off), Mp);
                         r = red64((uint64_t)rh * sh32 + rl, Mp);
                     }
-                    run[cb * 16 + e] = addm(run[cb * 16 + e], r, Mp);
+                    run[e] = (c > 0) ? addm(run[e], r, Mp) : r;
+                }
+                if (!last) {
+                    tmem_st8(tbase + NACC * BN, run);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < CW; ++e) tile[srow * BN + ((col + e) ^ (srow & 31))] = run[e];
                 }
             }
+            if (!last) tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar));
         }
-        // Every MMA has completed (the last accumulator barrier), so the operand
-        // stages are free: the tile goes through shared memory and C is read and
-        // written row by row with the lanes along the columns.
-        constexpr int LDT = BN + 1;
-        uint32_t *tile = (uint32_t *)smem;
+        if (pref) cp_async_wait_all();
+        // every epilogue warp has staged its rows (or given up)
+        epi_bar();
         if (ok) {
+            constexpr int B2 = 32;
 #pragma unroll
-            for (int e = 0; e < CPW; ++e) {
-                uint32_t v = run[e];
-                if (mont) v = redc((uint64_t)v * Mp.r2, Mp);      // v R
-                tile[trow * LDT + hcol * CPW + e] = v;
-            }
-        }
-        const int failed = epi_bar_or(ok ? 0 : 1);
-        if (!failed) {
-            // C is updated in batches of 32 elements per thread, each batch loaded
-            // completely before it is written back (one global round trip per batch)
-            constexpr int PER = BM * BN / (32 * NEPI), BATCH = 32;
-            const int et = threadIdx.x - 64;                  // 0 .. 32 NEPI - 1
+            for (int i0 = 0; i0 < PER; i0 += B2) {
+                uint32_t cv[B2];
 #pragma unroll
-            for (int b0 = 0; b0 < PER; b0 += BATCH) {
-                uint32_t cv[BATCH];
-#pragma unroll
-                for (int i = 0; i < BATCH; ++i) {
-                    const int e = et + 32 * NEPI * (b0 + i);
-                    const int rr = e / BN, cc = e % BN;
-                    cv[i] = (m0 + rr < M && n0 + cc < N) ? C[(int64_t)(m0 + rr) * ldc + n0 + cc] : 0u;
+                for (int i = 0; i < B2; ++i) {
+                    const int e = et + 32 * NEPI * (i0 + i), rr = e / BN, cc = e % BN;
+                    const bool in = m0 + rr < M && n0 + cc < N;
+                    cv[i] = !in ? 0u : pref ? cbuf[e] : C[(int64_t)(m0 + rr) * ldc + n0 + cc];
                 }
 #pragma unroll
-                for (int i = 0; i < BATCH; ++i) {
-                    const int e = et + 32 * NEPI * (b0 + i);
-                    const int rr = e / BN, cc = e % BN;
+                for (int i = 0; i < B2; ++i) {
+                    const int e = et + 32 * NEPI * (i0 + i), rr = e / BN, cc = e % BN;
                     if (m0 + rr < M && n0 + cc < N) {
-                        const uint32_t v = tile[rr * LDT + cc];
+                        const uint32_t v = tile[rr * BN + (cc ^ (rr & 31))];
                         C[(int64_t)(m0 + rr) * ldc + n0 + cc] = add ? addm(cv[i], v, Mp) : subm(cv[i], v, Mp);
                     }
                 }
@@ -415,53 +454,61 @@ __device__ __forceinline__ void split_digits(uint32_t x, uint32_t p, uint32_t ha
     d[L - 1] = __int2bfloat16_rn(v);
 }
 
+// One launch splits both operands: blocks [0, nbA) take rows of A (one thread:
+// 8 consecutive k of a row; planes (L, M, Kp_stride)), the rest take 32 x 32 tiles
+// of B through shared memory (planes (L, N_stride, Kp_stride), K-major). With
+// `mont`, A's residues are first multiplied by R (Montgomery form), which the
+// GEMM epilogue's single Montgomery reduction then removes.
 template <int L>
 __global__ void __launch_bounds__(256)
-k_split_rows(const GemmDesc d, int Kp_stride, uint32_t p, __nv_bfloat16 *__restrict__ out)
-{
-    // one thread: 8 consecutive k of one row of A; planes are (L, M, Kp_stride)
-    const int M = (int)d.M, K = (int)d.K.eval();
-    const int Kp = (K + BK - 1) / BK * BK;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int kv = Kp_stride / 8;
-    const int64_t i = idx / kv;
-    const int k0 = (int)(idx - i * kv) * 8;
-    if (i >= M || k0 >= Kp) return;
-    const uint32_t *A = d.A + (d.arow.eval() + i) * d.lda + d.acol.eval();
-    const uint32_t half = (p - 1) / 2;
-    __align__(16) __nv_bfloat16 buf[L][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int k = k0 + e;
-        __nv_bfloat16 dg[L];
-        split_digits<L>(k < K ? A[k] : 0u, p, half, dg);
-#pragma unroll
-        for (int l = 0; l < L; ++l) buf[l][e] = dg[l];
-    }
-    const int64_t plane = (int64_t)M * Kp_stride;
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-        *(uint4 *)(out + l * plane + i * Kp_stride + k0) = *(const uint4 *)buf[l];
-}
-
-// B (K x N) -> planes (L, N_stride, Kp_stride): 32 x 32 tiles through shared memory.
-template <int L>
-__global__ void __launch_bounds__(256)
-k_split_cols(const GemmDesc d, int N_stride, int Kp_stride, uint32_t p, __nv_bfloat16 *__restrict__ out)
+k_split(const GemmDesc d, int Kp_stride, int N_stride, int nbA, int gxB, ModP Mp, int mont,
+        __nv_bfloat16 *__restrict__ outA, __nv_bfloat16 *__restrict__ outB)
 {
     __shared__ uint32_t t[32][33];
-    const int K = (int)d.K.eval(), N = (int)d.N.eval();
+    const uint32_t p = Mp.p, half = (p - 1) / 2;
+    const int K = (int)d.K.eval();
     const int Kp = (K + BK - 1) / BK * BK;
-    const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    if ((int)blockIdx.x < nbA) {
+        const int M = (int)d.M;
+        const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int kv = Kp_stride / 8;
+        const int64_t i = idx / kv;
+        const int k0 = (int)(idx - i * kv) * 8;
+        if (i >= M || k0 >= Kp) return;
+        const uint32_t *A = d.A + (d.arow.eval() + i) * d.lda + d.acol.eval();
+        uint32_t x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = (k0 + e < K) ? A[k0 + e] : 0u;
+        __align__(16) __nv_bfloat16 buf[L][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t v = mont ? redc((uint64_t)x[e] * Mp.r2, Mp) : x[e];
+            __nv_bfloat16 dg[L];
+            split_digits<L>(v, p, half, dg);
+#pragma unroll
+            for (int l = 0; l < L; ++l) buf[l][e] = dg[l];
+        }
+        const int64_t plane = (int64_t)M * Kp_stride;
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            *(uint4 *)(outA + l * plane + i * Kp_stride + k0) = *(const uint4 *)buf[l];
+        return;
+    }
+    const int bb = (int)blockIdx.x - nbA;
+    const int N = (int)d.N.eval();
+    const int k0 = (bb / gxB) * 32, n0 = (bb % gxB) * 32;
     if (k0 >= Kp || n0 >= N) return;
     const uint32_t *B = d.B + d.brow.eval() * d.ldb + d.bcol.eval();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
-    for (int r = ty; r < 32; r += 8) {
-        const int k = k0 + r, n = n0 + tx;
-        t[r][tx] = (k < K && n < N) ? B[(int64_t)k * d.ldb + n] : 0u;
+    uint32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = k0 + ty + 8 * j, n = n0 + tx;
+        v[j] = (k < K && n < N) ? B[(int64_t)k * d.ldb + n] : 0u;
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[ty + 8 * j][tx] = v[j];
     __syncthreads();
-    const uint32_t half = (p - 1) / 2;
     const int64_t plane = (int64_t)N_stride * Kp_stride;
     for (int r = ty; r < 32; r += 8) {
         const int n = n0 + r, k = k0 + tx;
@@ -469,7 +516,7 @@ k_split_cols(const GemmDesc d, int N_stride, int Kp_stride, uint32_t p, __nv_bfl
             __nv_bfloat16 dg[L];
             split_digits<L>(t[tx][r], p, half, dg);
 #pragma unroll
-            for (int l = 0; l < L; ++l) out[l * plane + (int64_t)n * Kp_stride + k] = dg[l];
+            for (int l = 0; l < L; ++l) outB[l * plane + (int64_t)n * Kp_stride + k] = dg[l];
         }
     }
 }
@@ -511,10 +558,11 @@ cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
     __nv_bfloat16 *Al = (__nv_bfloat16 *)ws;
     __nv_bfloat16 *Bl = Al + (size_t)L * M * Kp;
     {
-        int64_t nthr = (int64_t)M * (Kp / 8);
-        k_split_rows<L><<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(d, Kp, Mp.p, Al);
-        dim3 g((Nmax + 31) / 32, (Kp + 31) / 32);
-        k_split_cols<L><<<g, 256, 0, st>>>(d, Nmax, Kp, Mp.p, Bl);
+        const int64_t nthr = (int64_t)M * (Kp / 8);
+        const int nbA = (int)((nthr + 255) / 256);
+        const int gxB = (Nmax + 31) / 32, gyB = (Kp + 31) / 32;
+        const int mont = (L <= 3) && (Mp.p & 1u);
+        k_split<L><<<(unsigned)(nbA + gxB * gyB), 256, 0, st>>>(d, Kp, Nmax, nbA, gxB, Mp, mont, Al, Bl);
     }
     CUtensorMap ta, tb;
     if (!make_map(&ta, Al, Kp, M, L, BM) || !make_map(&tb, Bl, Kp, Nmax, L, CF::BN))
