@@ -27,7 +27,7 @@ namespace tc {
 
 constexpr int BM = 128;       // rows per tile (tcgen05 M)
 constexpr int BK = 64;        // k per pipeline stage: one 128-byte swizzle row of bf16
-constexpr int NEPI = 8;       // epilogue warps (two per TMEM lane quarter)
+constexpr int NEPI = 16;      // epilogue warps (four per TMEM lane quarter)
 constexpr int NTHREADS = 32 * (2 + NEPI);
 constexpr int SMEM_BUDGET = 200 * 1024;
 
@@ -316,7 +316,7 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // (1) With a short K the C tile is copied asynchronously (coalesced) into
         // the shared memory the unused stages leave, while the MMAs run.
         // (2) Per chunk, warp w reads TMEM lane quarter w % 4 (one row per thread)
-        // and half of the columns, recombines the shift accumulators in 64 bits and
+        // and a quarter of the columns, recombines the shift accumulators in 64 bits and
         // reduces them; partial sums of earlier chunks wait in the TMEM columns
         // after the accumulators. (3) The reduced tile goes through stage 0 (free
         // once the last MMA has completed; XOR-swizzled rows keep both access
@@ -333,8 +333,8 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
         }
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
-        const int cg = (warp - 2) >> 2;                   // which half of the BN columns
-        constexpr int CPW = BN / 2;                       // columns per thread
+        const int cg = (warp - 2) >> 2;                   // which quarter of the BN columns
+        constexpr int CPW = BN / 4;                       // columns per thread
         constexpr int CW = 8;                             // columns per TMEM load
         const uint32_t trow = (uint32_t)(32 * q) << 16;
         const int srow = 32 * q + lane;                   // this thread's row of the tile
@@ -407,22 +407,27 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // every epilogue warp has staged its rows (or given up)
         epi_bar();
         if (ok) {
-            constexpr int B2 = 32;
+            // thread et owns column cc of rows rr0, rr0 + RPI, ...: addresses advance by a fixed step
+            constexpr int RPI = 32 * NEPI / BN, B2 = 8;
+            const int rr0 = et / BN, cc = et % BN;
+            const bool colok = n0 + cc < N;
+            const int64_t step = (int64_t)RPI * ldc;
+            uint32_t *cp = C + (int64_t)(m0 + rr0) * ldc + n0 + cc;
 #pragma unroll
             for (int i0 = 0; i0 < PER; i0 += B2) {
                 uint32_t cv[B2];
+                const uint32_t *lp = cp;
 #pragma unroll
-                for (int i = 0; i < B2; ++i) {
-                    const int e = et + 32 * NEPI * (i0 + i), rr = e / BN, cc = e % BN;
-                    const bool in = m0 + rr < M && n0 + cc < N;
-                    cv[i] = !in ? 0u : pref ? cbuf[e] : C[(int64_t)(m0 + rr) * ldc + n0 + cc];
+                for (int i = 0; i < B2; ++i, lp += step) {
+                    const bool in = colok && m0 + rr0 + RPI * (i0 + i) < M;
+                    cv[i] = !in ? 0u : pref ? cbuf[et + 32 * NEPI * (i0 + i)] : *lp;
                 }
 #pragma unroll
-                for (int i = 0; i < B2; ++i) {
-                    const int e = et + 32 * NEPI * (i0 + i), rr = e / BN, cc = e % BN;
-                    if (m0 + rr < M && n0 + cc < N) {
+                for (int i = 0; i < B2; ++i, cp += step) {
+                    const int rr = rr0 + RPI * (i0 + i);
+                    if (colok && m0 + rr < M) {
                         const uint32_t v = tile[rr * BN + (cc ^ (rr & 31))];
-                        C[(int64_t)(m0 + rr) * ldc + n0 + cc] = add ? addm(cv[i], v, Mp) : subm(cv[i], v, Mp);
+                        *cp = add ? addm(cv[i], v, Mp) : subm(cv[i], v, Mp);
                     }
                 }
             }

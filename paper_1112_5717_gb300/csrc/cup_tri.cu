@@ -225,9 +225,19 @@ k_trsm_ruu128(const TriDesc d, ModP M)
     cp_async_wait_all();
     __syncthreads();
     if (MONT)
-        for (int idx = threadIdx.x; idx < n * RUU_MAX; idx += blockDim.x) {
-            const int k = idx >> 7, j = idx & (RUU_MAX - 1);
-            if (j > k && j < n) sU[k * RUU_LDS + j] = to_mont<MONT>(sU[k * RUU_LDS + j], M);
+        for (int base = threadIdx.x; base < n * RUU_MAX; base += 8 * blockDim.x) {
+            // eight independent entries per pass (all read before any is written)
+            uint32_t v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int idx = base + e * blockDim.x, k = idx >> 7, j = idx & (RUU_MAX - 1);
+                v[e] = (idx < n * RUU_MAX && j > k && j < n) ? sU[k * RUU_LDS + j] : 0u;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int idx = base + e * blockDim.x, k = idx >> 7, j = idx & (RUU_MAX - 1);
+                if (idx < n * RUU_MAX && j > k && j < n) sU[k * RUU_LDS + j] = to_mont<MONT>(v[e], M);
+            }
         }
     __syncthreads();
     const int lane = threadIdx.x & 31;
