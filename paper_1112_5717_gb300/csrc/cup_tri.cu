@@ -194,7 +194,7 @@ cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t 
 // Algorithm 6): one warp per row of B, each lane holding columns lane + 32 k;
 // at step k the final x_k is broadcast and the later columns subtract x_k u_kj.
 #define RUU_MAX 128
-#define RUU_LDS (RUU_MAX + 1)
+#define RUU_LDS (RUU_MAX + 4)   // 16-byte aligned rows
 // Montgomery reduction of T < 2 p R (p < 2^24) to [0, p): the raw result is below 3p.
 __device__ __forceinline__ uint32_t redc_lazy(uint64_t T, const ModP &M)
 {
@@ -205,42 +205,65 @@ __device__ __forceinline__ uint32_t redc_lazy(uint64_t T, const ModP &M)
     return t;
 }
 
-template <bool MONT, bool LAZY>
+// x mod p for x < 2^39 and p < 2^16: the bits from 24 up are folded with 2^24 mod p
+// (the sum stays below 2^32), then one 32-bit Barrett step with mu32 = floor(2^32 / p).
+__device__ __forceinline__ uint32_t red39(uint64_t x, uint32_t p, uint32_t c24, uint32_t mu32)
+{
+    uint32_t t = (uint32_t)(x >> 24) * c24 + (uint32_t)(x & 0xffffffu);
+    t -= __umulhi(t, mu32) * p;
+    return t >= p ? t - p : t;
+}
+
+// MODE 0: per-step Montgomery products (any odd p); 1: lazy Montgomery accumulation
+// (odd p < 2^24, the triangle in Montgomery form); 2: lazy plain accumulation
+// (p < 2^16, the triangle as it is, products below 2^32 and sums below 2^39).
+template <int MODE>
 __global__ void __launch_bounds__(256)
 k_trsm_ruu128(const TriDesc d, ModP M)
 {
-    extern __shared__ uint32_t sU[];                      // RUU_MAX x RUU_LDS, Montgomery form
+    constexpr bool MONT = MODE <= 1, LAZY = MODE >= 1;
+    extern __shared__ __align__(16) uint32_t sU[];        // RUU_MAX x RUU_LDS
     const int n = (int)d.n.eval();
     if (n <= 0) return;
     const int64_t m = d.rows, ldt = d.ldt, ldb = d.ldb;
     const uint32_t *__restrict__ T = d.T + d.trow.eval() * ldt + d.tcol.eval();
     uint32_t *__restrict__ B = d.B + d.brow.eval() * ldb + d.bcol.eval();
-    // strictly upper part of the n x n block by asynchronous copies, zeros elsewhere
-    // (rows >= n are never read); then the copied entries to Montgomery form
-    for (int idx = threadIdx.x; idx < n * RUU_MAX; idx += blockDim.x) {
-        const int k = idx >> 7, j = idx & (RUU_MAX - 1);
-        if (j > k && j < n) cp_async4(sU + k * RUU_LDS + j, T + k * ldt + j);
-        else sU[k * RUU_LDS + j] = 0u;
+    // rows 0 .. n-1 of the triangle by asynchronous copies (16-byte pieces when the
+    // rows are 16-byte aligned), then one pass keeping only the strictly upper part
+    // (zeros elsewhere; rows >= n are never read), in Montgomery form for MODE <= 1
+    if (((uintptr_t)T & 15u) == 0 && (ldt & 3) == 0) {
+        const int nv = n >> 2;                            // whole 16-byte pieces per row
+        for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+            const int k = idx >> 5, v = idx & 31;
+            if (v < nv) cp_async16(sU + k * RUU_LDS + 4 * v, T + k * ldt + 4 * v);
+            else if (v == nv)                             // the ragged end of the row, word by word
+                for (int j = 4 * nv; j < n; ++j) cp_async4(sU + k * RUU_LDS + j, T + k * ldt + j);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < n * RUU_MAX; idx += blockDim.x) {
+            const int k = idx >> 7, j = idx & (RUU_MAX - 1);
+            if (j < n) cp_async4(sU + k * RUU_LDS + j, T + k * ldt + j);
+        }
     }
     cp_async_wait_all();
     __syncthreads();
-    if (MONT)
-        for (int base = threadIdx.x; base < n * RUU_MAX; base += 8 * blockDim.x) {
-            // eight independent entries per pass (all read before any is written)
-            uint32_t v[8];
+    for (int base = threadIdx.x; base < n * RUU_MAX; base += 8 * blockDim.x) {
+        // eight independent entries per pass (all read before any is written)
+        uint32_t v[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int idx = base + e * blockDim.x, k = idx >> 7, j = idx & (RUU_MAX - 1);
-                v[e] = (idx < n * RUU_MAX && j > k && j < n) ? sU[k * RUU_LDS + j] : 0u;
-            }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int idx = base + e * blockDim.x, k = idx >> 7, j = idx & (RUU_MAX - 1);
-                if (idx < n * RUU_MAX && j > k && j < n) sU[k * RUU_LDS + j] = to_mont<MONT>(v[e], M);
-            }
+        for (int e = 0; e < 8; ++e) {
+            const int idx = base + e * blockDim.x, k = idx >> 7, j = idx & (RUU_MAX - 1);
+            v[e] = (idx < n * RUU_MAX && j > k && j < n) ? sU[k * RUU_LDS + j] : 0u;
         }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = base + e * blockDim.x, k = idx >> 7, j = idx & (RUU_MAX - 1);
+            if (idx < n * RUU_MAX) sU[k * RUU_LDS + j] = MONT ? to_mont<MONT>(v[e], M) : v[e];
+        }
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const uint32_t c24 = (uint32_t)((1u << 24) % M.p), mu32 = (uint32_t)(0xffffffffu / M.p);
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nw) {
         uint32_t *row = B + i * ldb;
@@ -249,17 +272,18 @@ k_trsm_ruu128(const TriDesc d, ModP M)
             // only column k is reduced at step k (one Montgomery reduction on the chain).
             // With p < 2^24 the sum stays below p R + 128 p^2 < 2 p R, so the
             // reduction lands in [0, 3p).
+            // MODE 2: the same accumulation without the factor R (b_j + sum (p - x_k) u_kj < 2^39)
             uint64_t acc[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                acc[c] = (lane + 32 * c < n) ? ((uint64_t)row[lane + 32 * c] << 32) : 0ull;
+                acc[c] = (lane + 32 * c < n) ? ((uint64_t)row[lane + 32 * c] << (MODE == 2 ? 0 : 32)) : 0ull;
 #pragma unroll
             for (int cb = 0; cb < 4; ++cb) {
                 if (32 * cb >= n) break;
                 const int kend = n - 32 * cb < 32 ? n - 32 * cb : 32;
                 for (int kk = 0; kk < kend; ++kk) {
                     const int k = 32 * cb + kk;
-                    uint32_t t = redc_lazy(acc[cb], M);
+                    const uint32_t t = (MODE == 2) ? red39(acc[cb], M.p, c24, mu32) : redc_lazy(acc[cb], M);
                     const uint32_t xk = __shfl_sync(0xffffffffu, t, kk);
                     const uint32_t nx = xk ? M.p - xk : 0u;
                     const uint32_t *uk = sU + k * RUU_LDS + lane;
@@ -269,7 +293,8 @@ k_trsm_ruu128(const TriDesc d, ModP M)
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                if (lane + 32 * c < n) row[lane + 32 * c] = redc_lazy(acc[c], M);
+                if (lane + 32 * c < n)
+                    row[lane + 32 * c] = (MODE == 2) ? red39(acc[c], M.p, c24, mu32) : redc_lazy(acc[c], M);
         } else {
             uint32_t x[4];
 #pragma unroll
@@ -297,19 +322,19 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
     static bool attr = false;
     const size_t smem = (size_t)RUU_MAX * RUU_LDS * sizeof(uint32_t);
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm_ruu128<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(k_trsm_ruu128<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm_ruu128<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(k_trsm_ruu128<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     int64_t nb = (d.rows + 7) / 8;
     if (nb > 152 * 8) nb = 152 * 8;
-    if ((M.p & 1u) && M.p < (1u << 24)) k_trsm_ruu128<true, true><<<(unsigned)nb, 256, smem, st>>>(d, M);
-    else if (M.p & 1u) k_trsm_ruu128<true, false><<<(unsigned)nb, 256, smem, st>>>(d, M);
-    else k_trsm_ruu128<false, false><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    if (M.p < (1u << 16)) k_trsm_ruu128<2><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    else if (M.p < (1u << 24)) k_trsm_ruu128<1><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    else k_trsm_ruu128<0><<<(unsigned)nb, 256, smem, st>>>(d, M);
     return cudaGetLastError();
 }
 
