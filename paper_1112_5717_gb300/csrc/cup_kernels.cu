@@ -329,7 +329,9 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                     }
                     s_coef[k][s] = cf;
                     // the row's own column of E only picks up the scale
-                    if (s == 0) E[k * PIV_LDE + k] = mulm(E[k * PIV_LDE + k], A0f, M);
+                    if (s == 0)
+                        E[k * PIV_LDE + k] = (MONT && !WIDE) ? redc((uint64_t)E[k * PIV_LDE + k] * A0, M)   // A0 is A0 R here
+                                                             : mulm(E[k * PIV_LDE + k], A0f, M);
                 }
             }
             __syncthreads();
@@ -387,19 +389,22 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     }
     __syncthreads();
     if (warp == 0) {
-        // exclusive prefix products Sinv[t] = prod_{t' < t} mu_{t'}^{-1}
-        uint32_t carry = one;
+        // exclusive prefix products Sinv[t] = prod_{t' < t} mu_{t'}^{-1}; for odd p kept in
+        // Montgomery representation (Sinv R), products by Montgomery steps
+        const uint32_t oneR = MONT ? redc((uint64_t)M.r2, M) : one;
+        uint32_t carry = oneR;
         for (int base = 0; base < rs; base += 32) {
             const int t = base + lane;
-            uint32_t v = (t < rs) ? s_muinv[t] : one;
+            uint32_t v = (t < rs) ? (MONT ? redc((uint64_t)s_muinv[t] * M.r2, M) : s_muinv[t]) : oneR;
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v = mulm(v, u, M);
+                if (lane >= o) v = MONT ? redc((uint64_t)v * u, M) : mulm(v, u, M);
             }
             uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
-            if (lane == 0) ex = one;
-            if (t < rs) s_Sinv[t] = mulm(carry, ex, M);
-            carry = mulm(carry, __shfl_sync(0xffffffffu, v, 31), M);
+            if (lane == 0) ex = oneR;
+            if (t < rs) s_Sinv[t] = MONT ? redc((uint64_t)carry * ex, M) : mulm(carry, ex, M);
+            const uint32_t last = __shfl_sync(0xffffffffu, v, 31);
+            carry = MONT ? redc((uint64_t)carry * last, M) : mulm(carry, last, M);
         }
     }
     __syncthreads();
@@ -407,23 +412,30 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     // C values of the resolved rows: W[i][t] carries the scale S_t of step t.
     // L^{-1} for the finish kernel: pivot row t of the eliminated slab is
     // (E X)_t = f_t U_t, so U = diag(1/f) E_pp X over the pivot rows, i.e.
-    // L^{-1}[t][u] = E[prof t][prof u] / f_t (zero for u > t).
+    // L^{-1}[t][u] = E[prof t][prof u] / f_t (zero for u > t). For odd p the
+    // factors are Montgomery representations (Sinv R, and f^{-1} R = mu^{-1}),
+    // so each entry is one Montgomery step.
     {
         const int t = tid & (CUP_BMAX - 1);
         if (t < rs) {
             const int pt = s_prof[t];
             const uint32_t sinv = s_Sinv[t];
-            for (int i = tid >> 6; i < stop; i += nt >> 6)
-                S->Cn[i][t] = (i >= pt) ? mulm(W[i * PIV_LDW + t], sinv, M) : 0u;
+            for (int i = tid >> 6; i < stop; i += nt >> 6) {
+                const uint32_t wv = W[i * PIV_LDW + t];
+                S->Cn[i][t] = (i >= pt) ? (MONT ? redc((uint64_t)wv * sinv, M) : mulm(wv, sinv, M)) : 0u;
+            }
         }
         const int u = tid & (CUP_BMAX - 1);
         if (u < rs) {
             const int pu = s_prof[u];
-            for (int t2 = tid >> 6; t2 < rs; t2 += nt >> 6)
-                S->Linv[t2][u] = mulm(E[s_prof[t2] * PIV_LDE + pu], s_finv[t2], M);
+            for (int t2 = tid >> 6; t2 < rs; t2 += nt >> 6) {
+                const uint32_t ev = E[s_prof[t2] * PIV_LDE + pu];
+                S->Linv[t2][u] = MONT ? redc((uint64_t)ev * s_muinv[t2], M) : mulm(ev, s_finv[t2], M);
+            }
         }
     }
-    for (int t = tid; t < rs; t += nt) S->pinv[t] = mulm(s_Sfwd[t], s_finv[t], M);
+    for (int t = tid; t < rs; t += nt)
+        S->pinv[t] = MONT ? redc((uint64_t)s_Sfwd[t] * s_muinv[t], M) : mulm(s_Sfwd[t], s_finv[t], M);
     if (warp == 0) {
         int ns = 0;
         for (int base = 0; base < wne; base += 32) {

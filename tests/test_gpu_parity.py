@@ -50,6 +50,27 @@ def test_trsm_ruu(cuda_lib, m, n, p):
     assert np.array_equal(_host(dB), want)
 
 
+@pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
+@pytest.mark.parametrize("ld,off", [(100, 0), (101, 1)])
+def test_trsm_ruu_strided_triangle(cuda_lib, p, ld, off):
+    """The triangle as a view with row stride ld (16-byte aligned rows when ld = 100 and the
+    view starts at column 0; unaligned otherwise) and n = 97, so a row ends with a partial
+    16-byte piece; every accumulation mode of the leaf (p below 2^16, 2^24, 2^31)."""
+    n, m = 97, 150
+    rng = np.random.default_rng(ld * 7 + p % 1000)
+    U = rng.integers(0, p, size=(n, n))
+    B = rng.integers(0, p, size=(m, n))
+    want = oracle.trsm_right_upper_unit(U, B, p)
+    big = np.zeros((n, ld + off), dtype=np.uint32)
+    big[:, off:off + n] = U
+    dbig = _dev(big)
+    dU = dbig[:, off:off + n]
+    dB = _dev(B)
+    cuda_lib.trsm_ruu(dU, dB, p)
+    assert np.array_equal(_host(dB), want)
+    assert np.array_equal(_host(dbig), big)          # the triangle is only read
+
+
 def test_laswp_cols(cuda_lib):
     import torch
     rng = np.random.default_rng(1)
