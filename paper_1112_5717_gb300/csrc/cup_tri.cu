@@ -195,6 +195,7 @@ cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t 
 // at step k the final x_k is broadcast and the later columns subtract x_k u_kj.
 #define RUU_MAX 128
 #define RUU_LDS (RUU_MAX + 4)   // 16-byte aligned rows
+#define TRI_VLD 33               // row stride of the 32 x 32 block inverses
 // Montgomery reduction of T < 2 p R (p < 2^24) to [0, p): the raw result is below 3p.
 __device__ __forceinline__ uint32_t redc_lazy(uint64_t T, const ModP &M)
 {
@@ -215,13 +216,14 @@ __device__ __forceinline__ uint32_t red39(uint64_t x, uint32_t p, uint32_t c24, 
 }
 
 // MODE 0: per-step Montgomery products (any odd p); 1: lazy Montgomery accumulation
-// (odd p < 2^24, the triangle in Montgomery form); 2: lazy plain accumulation
-// (p < 2^16, the triangle as it is, products below 2^32 and sums below 2^39).
+// (odd p < 2^24, the triangle in Montgomery form); 3: p < 2^16, the triangle as it is,
+// each 32-column block solved with the inverse of its diagonal block and plain lazy
+// sums (products below 2^32, sums below 2^39).
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_trsm_ruu128(const TriDesc d, ModP M)
 {
-    constexpr bool MONT = MODE <= 1, LAZY = MODE >= 1;
+    constexpr bool MONT = MODE <= 1, LAZY = MODE == 1;
     extern __shared__ __align__(16) uint32_t sU[];        // RUU_MAX x RUU_LDS
     const int n = (int)d.n.eval();
     if (n <= 0) return;
@@ -264,26 +266,90 @@ k_trsm_ruu128(const TriDesc d, ModP M)
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t c24 = (uint32_t)((1u << 24) % M.p), mu32 = (uint32_t)(0xffffffffu / M.p);
+    // MODE 3: V_b = inverse of the b-th 32 x 32 diagonal block (unit upper), by warp b;
+    // lane j keeps column j in registers and runs the back substitution
+    // V[k][j] = -sum_{l > k} U[k][l] V[l][j] from the bottom row up (rows past n stay
+    // identity rows)
+    uint32_t *const sV = sU + RUU_MAX * RUU_LDS;
+    if (MODE == 3) {
+        const int wv = threadIdx.x >> 5;
+        if (wv < 4 && 32 * wv < n) {
+            const int b0 = 32 * wv;
+            const int nbr = n - b0 < 32 ? n - b0 : 32;
+            uint32_t v[32];
+#pragma unroll
+            for (int l = 0; l < 32; ++l) v[l] = (l == lane) ? 1u : 0u;
+#pragma unroll
+            for (int k = 30; k >= 0; --k) {
+                if (k < nbr) {
+                    const uint32_t *uk = sU + (b0 + k) * RUU_LDS + b0;
+                    uint64_t sum = 0;
+#pragma unroll
+                    for (int l = k + 1; l < 32; ++l) sum += (uint64_t)uk[l] * v[l];
+                    const uint32_t r = red39(sum, M.p, c24, mu32);
+                    if (k < lane) v[k] = r ? M.p - r : 0u;
+                }
+            }
+            uint32_t *V = sV + wv * 32 * TRI_VLD;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) V[k * TRI_VLD + lane] = v[k];
+        }
+        __syncthreads();
+    }
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nw) {
         uint32_t *row = B + i * ldb;
-        if (LAZY) {
+        if (MODE == 3) {
+            // X_b = (B_b - sum_{a < b} X_a U_ab) V_b: the block's solve is 32 independent
+            // products per lane (no dependency chain), then the block's values update the
+            // later blocks; plain lazy sums (below 2^39) reduced by the 39-bit fold
+            uint64_t acc[4];
+            uint32_t xo[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                acc[c] = (lane + 32 * c < n) ? (uint64_t)row[lane + 32 * c] : 0ull;
+                xo[c] = 0u;
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (32 * b >= n) break;
+                const uint32_t y = red39(acc[b], M.p, c24, mu32);
+                const uint32_t *V = sV + b * 32 * TRI_VLD + lane;
+                uint64_t sum = 0;
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sum += (uint64_t)__shfl_sync(0xffffffffu, y, k) * V[k * TRI_VLD];
+                const uint32_t x = red39(sum, M.p, c24, mu32);
+                xo[b] = x;
+                if (b < 3 && 32 * (b + 1) < n) {
+                    const uint32_t nx = x ? M.p - x : 0u;
+                    const uint32_t *ub = sU + 32 * b * RUU_LDS + lane;
+#pragma unroll 4
+                    for (int k = 0; k < 32; ++k) {
+                        const uint64_t nk = __shfl_sync(0xffffffffu, nx, k);
+#pragma unroll
+                        for (int c = b + 1; c < 4; ++c) acc[c] += nk * ub[k * RUU_LDS + 32 * c];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (lane + 32 * c < n) row[lane + 32 * c] = xo[c];
+        } else if (LAZY) {
             // x_j = b_j - sum_{k<j} x_k u_kj accumulated unreduced as R b_j + sum (p - x_k) (R u_kj):
             // only column k is reduced at step k (one Montgomery reduction on the chain).
             // With p < 2^24 the sum stays below p R + 128 p^2 < 2 p R, so the
             // reduction lands in [0, 3p).
-            // MODE 2: the same accumulation without the factor R (b_j + sum (p - x_k) u_kj < 2^39)
             uint64_t acc[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                acc[c] = (lane + 32 * c < n) ? ((uint64_t)row[lane + 32 * c] << (MODE == 2 ? 0 : 32)) : 0ull;
+                acc[c] = (lane + 32 * c < n) ? ((uint64_t)row[lane + 32 * c] << 32) : 0ull;
 #pragma unroll
             for (int cb = 0; cb < 4; ++cb) {
                 if (32 * cb >= n) break;
                 const int kend = n - 32 * cb < 32 ? n - 32 * cb : 32;
                 for (int kk = 0; kk < kend; ++kk) {
                     const int k = 32 * cb + kk;
-                    const uint32_t t = (MODE == 2) ? red39(acc[cb], M.p, c24, mu32) : redc_lazy(acc[cb], M);
+                    const uint32_t t = redc_lazy(acc[cb], M);
                     const uint32_t xk = __shfl_sync(0xffffffffu, t, kk);
                     const uint32_t nx = xk ? M.p - xk : 0u;
                     const uint32_t *uk = sU + k * RUU_LDS + lane;
@@ -293,8 +359,7 @@ k_trsm_ruu128(const TriDesc d, ModP M)
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                if (lane + 32 * c < n)
-                    row[lane + 32 * c] = (MODE == 2) ? red39(acc[c], M.p, c24, mu32) : redc_lazy(acc[c], M);
+                if (lane + 32 * c < n) row[lane + 32 * c] = redc_lazy(acc[c], M);
         } else {
             uint32_t x[4];
 #pragma unroll
@@ -320,19 +385,19 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
     if (d.rows <= 0 || d.n.hi <= 0) return cudaSuccess;
     if (d.n.hi > RUU_MAX) return cudaErrorInvalidValue;
     static bool attr = false;
-    const size_t smem = (size_t)RUU_MAX * RUU_LDS * sizeof(uint32_t);
+    const size_t smem = ((size_t)RUU_MAX * RUU_LDS + 4 * 32 * TRI_VLD) * sizeof(uint32_t);
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_trsm_ruu128<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm_ruu128<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(k_trsm_ruu128<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     int64_t nb = (d.rows + 7) / 8;
     if (nb > 152 * 8) nb = 152 * 8;
-    if (M.p < (1u << 16)) k_trsm_ruu128<2><<<(unsigned)nb, 256, smem, st>>>(d, M);
+    if (M.p < (1u << 16)) k_trsm_ruu128<3><<<(unsigned)nb, 256, smem, st>>>(d, M);
     else if (M.p < (1u << 24)) k_trsm_ruu128<1><<<(unsigned)nb, 256, smem, st>>>(d, M);
     else k_trsm_ruu128<0><<<(unsigned)nb, 256, smem, st>>>(d, M);
     return cudaGetLastError();
