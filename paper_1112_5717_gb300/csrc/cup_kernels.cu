@@ -46,7 +46,7 @@
 #ifndef PIV_PB
 #define PIV_PB 8                    // panel rows of the blocked window elimination
 #endif
-#define PIV_PW 8                    // warps that eliminate a panel
+#define PIV_PW 16                   // warps that eliminate a panel (all of them: 8 column chunks x 2 row parities)
 
 // One fraction-free update f x - m y, scaled by R^{-1} in the Montgomery
 // variant (odd p): the common factor only changes the tracked row scales.
@@ -175,8 +175,9 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         if (warp < PIV_PW) {
             // Panel of rows [p0, pend), eliminated by the first PIV_PW warps (named
             // barrier 1): the rows are taken one by one as in the unblocked
-            // elimination, each step updating only the panel's rows. Warp w owns
-            // the 32-column chunk w of (window positions > r, then E columns [0, pend)).
+            // elimination, each step updating only the panel's rows. Warp w owns the
+            // 32-column chunk w % 8 of (window positions > r, then E columns [0, pend))
+            // in every other row below the pivot row.
             int lim = brows;                   // rows that still need this panel's pivots
             bool swapped = false;
             for (int i = p0; i < pend; ++i) {
@@ -210,21 +211,27 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                     s_prof[r] = i; s_f[r] = f; s_Sfwd[r] = Sprod;
                 }
                 const int nwc = wne - r - 1;
-                const int ci = 32 * warp + lane;
+                const int ci = 32 * (warp & 7) + lane;         // 32-column chunk of this warp
+                const int h = warp >> 3;                       // rows i + 1 + h, i + 3 + h, ...
                 if (ci < nwc + pend) {
-                    // every operand of the (at most PIV_PB - 1) rows is read before any result is stored
+                    // every operand of the rows is read before any result is stored
                     const bool inw = ci < nwc;
                     const uint32_t y = inw ? W[i * PIV_LDW + r + 1 + ci] : E[i * PIV_LDE + ci - nwc];
                     uint32_t *xk = inw ? W + (i + 1) * PIV_LDW + r + 1 + ci : E + (i + 1) * PIV_LDE + ci - nwc;
                     const int xs = inw ? PIV_LDW : PIV_LDE;
                     const int nk = pend - 1 - i;
-                    uint32_t mk[PIV_PB - 1], xv[PIV_PB - 1];
+                    constexpr int NJ = PIV_PB / 2;
+                    uint32_t mk[NJ], xv[NJ];
 #pragma unroll
-                    for (int j = 0; j < PIV_PB - 1; ++j)
-                        if (j < nk) { mk[j] = W[(i + 1 + j) * PIV_LDW + r]; xv[j] = xk[j * xs]; }
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        const int j = h + 2 * jj;
+                        if (j < nk) { mk[jj] = W[(i + 1 + j) * PIV_LDW + r]; xv[jj] = xk[j * xs]; }
+                    }
 #pragma unroll
-                    for (int j = 0; j < PIV_PB - 1; ++j)
-                        if (j < nk) xk[j * xs] = ff<MONT>(f, xv[j], mk[j], y, M);
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        const int j = h + 2 * jj;
+                        if (j < nk) xk[j * xs] = ff<MONT>(f, xv[jj], mk[jj], y, M);
+                    }
                 }
                 panel_bar();
                 Sprod = scale_mul<MONT>(Sprod, f, M);
