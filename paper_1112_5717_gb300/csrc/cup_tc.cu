@@ -186,10 +186,13 @@ __device__ __forceinline__ uint32_t redc_raw(uint64_t x, const ModP &M)
 }
 
 
-template <int L>
+template <int L, int BNX = 0>
 struct Cfg {
     static constexpr int NACC = 2 * L - 1;
-    static constexpr int BN = (NACC * 128 <= 512) ? 128 : 64;
+    static constexpr int BN = BNX ? BNX : ((NACC * 128 <= 512) ? 128 : 64);
+    // two accumulator sets (the MMAs of chunk c + 1 run while chunk c is drained) when
+    // they fit in TMEM next to the partial sums
+    static constexpr int NBUF = (2 * NACC * BN + BN <= 512) ? 2 : 1;
     static constexpr int STAGE_A = BM * BK * 2;
     static constexpr int STAGE_B = BN * BK * 2;
     static constexpr int STAGE = L * (STAGE_A + STAGE_B);
@@ -203,7 +206,7 @@ struct Cfg {
 };
 
 // C[M x N] -= A B (mod p) from limb planes: Al is (L, M, Kp), Bl is (L, N, Kp), bf16, K-major.
-template <int L>
+template <int L, int BNX>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const GemmDesc d, ModP Mp, uint64_t off, uint32_t sh32, int *__restrict__ err)
@@ -212,12 +215,12 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int Kp = (K + BK - 1) / BK * BK;
     const int add = d.add;
     const int64_t ldc = d.ldc;
-    if ((int)blockIdx.x * Cfg<L>::BN >= N || K <= 0) return;       // outside this call's extents
+    using CF = Cfg<L, BNX>;
+    if ((int)blockIdx.x * CF::BN >= N || K <= 0) return;       // outside this call's extents
     uint32_t *C = d.C + d.crow.eval() * ldc + d.ccol.eval();
-    using CF = Cfg<L>;
-    constexpr int BN = CF::BN, NACC = CF::NACC, NSTAGE = CF::NSTAGE;
+    constexpr int BN = CF::BN, NACC = CF::NACC, NSTAGE = CF::NSTAGE, NBUF = CF::NBUF;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], accf_bar, acce_bar;
+    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], accf_bar[NBUF], acce_bar[NBUF];
     __shared__ uint32_t tmem_base_sh;
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -236,8 +239,10 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&accf_bar), 1);
-        mbar_init(smem_u32(&acce_bar), NEPI);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), NEPI);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -281,8 +286,15 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int kb = 0;
             bool ok = true;
             for (int c = 0; c < nchunk && ok; ++c) {
-                if (c > 0 && !mbar_wait(smem_u32(&acce_bar), (uint32_t)(c - 1) & 1u, err, 3)) { ok = false; break; }
+                // accumulator set c % NBUF must have been drained (chunk c - NBUF)
+                const int buf = c % NBUF;
+                if (c >= NBUF &&
+                    !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)((c - NBUF) / NBUF) & 1u, err, 3)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
+                const uint32_t dbase = tmem + (uint32_t)(buf * NACC * BN);
                 const int kb_first = kb;
                 const int kb_end = (kb + kb_chunk < nkb) ? kb + kb_chunk : nkb;
                 for (; kb < kb_end; ++kb) {
@@ -302,13 +314,13 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                             for (int kk = 0; kk < BK / 16; ++kk) {
                                 const uint32_t acc = (kb == kb_first && i == ifirst && kk == 0) ? 0u : 1u;
-                                mma_bf16(tmem + sh * BN, sw128_desc(a_addr + kk * 32),
+                                mma_bf16(dbase + sh * BN, sw128_desc(a_addr + kk * 32),
                                          sw128_desc(b_addr + kk * 32), idesc, acc);
                             }
                         }
                     mma_commit(smem_u32(&empty_bar[s]));
                 }
-                if (ok) mma_commit(smem_u32(&accf_bar));
+                if (ok) mma_commit(smem_u32(&accf_bar[buf]));
             }
         }
     } else {
@@ -346,20 +358,22 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         uint32_t *tile = (uint32_t *)smem;
         bool ok = true;
         for (int c = 0; c < nchunk; ++c) {
-            if (!mbar_wait(smem_u32(&accf_bar), (uint32_t)c & 1u, err, 5)) { ok = false; break; }
+            const int buf = c % NBUF;
+            if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)(c / NBUF) & 1u, err, 5)) { ok = false; break; }
             tc_fence_after();
             const bool last = c == nchunk - 1;
 #pragma unroll
             for (int cb = 0; cb < CPW / CW; ++cb) {
                 const int col = cg * CPW + cb * CW;
-                const uint32_t tbase = tmem + trow + (uint32_t)col;
+                const uint32_t tbase = tmem + trow + (uint32_t)(buf * NACC * BN + col);
+                const uint32_t pbase = tmem + trow + (uint32_t)(NBUF * NACC * BN + col);   // partial sums
                 float d[NACC][CW];
 #pragma unroll
                 for (int s = 0; s < NACC; ++s) tmem_ld8(tbase + s * BN, d[s]);
                 uint32_t run[CW];
                 if (c > 0) {
                     float rf[CW];
-                    tmem_ld8(tbase + NACC * BN, rf);
+                    tmem_ld8(pbase, rf);
 #pragma unroll
                     for (int e = 0; e < CW; ++e) run[e] = __float_as_uint(rf[e]);
                 }
@@ -392,7 +406,7 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     run[e] = (c > 0) ? addm(run[e], r, Mp) : r;
                 }
                 if (!last) {
-                    tmem_st8(tbase + NACC * BN, run);
+                    tmem_st8(pbase, run);
                 } else {
 #pragma unroll
                     for (int e = 0; e < CW; ++e) tile[srow * BN + ((col + e) ^ (srow & 31))] = run[e];
@@ -401,7 +415,7 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (!last) tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&acce_bar));
+            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
         }
         if (pref) cp_async_wait_all();
         // every epilogue warp has staged its rows (or given up)
@@ -554,10 +568,11 @@ bool make_map(CUtensorMap *map, void *base, int kp, int rows, int L, int box_row
     return r == CUDA_SUCCESS;
 }
 
-template <int L>
-cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
+template <int L, int BNX>
+cudaError_t run_cfg(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0,
+                    cudaEvent_t ev1)
 {
-    using CF = Cfg<L>;
+    using CF = Cfg<L, BNX>;
     const int M = (int)d.M, Nmax = (int)d.N.hi, Kmax = (int)d.K.hi;
     const int Kp = (Kmax + BK - 1) / BK * BK;                    // plane row stride
     __nv_bfloat16 *Al = (__nv_bfloat16 *)ws;
@@ -574,7 +589,7 @@ cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_limb_gemm<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_limb_gemm<L, BNX>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -584,10 +599,18 @@ cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
     const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
     dim3 grid((Nmax + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
     if (ev0) cudaEventRecord(ev0, st);
-    k_limb_gemm<L><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, d, Mp, off, sh32, err);
+    k_limb_gemm<L, BNX><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, d, Mp, off, sh32, err);
     cudaError_t e = cudaGetLastError();
     if (ev1) cudaEventRecord(ev1, st);
     return e;
+}
+
+// (64-column tiles would let two-limb accumulators double-buffer too, but they need
+// half again the operand traffic per product and measured slower than 128 columns.)
+template <int L>
+cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    return run_cfg<L, 0>(d, Mp, ws, err, st, ev0, ev1);
 }
 
 }  // namespace tc
