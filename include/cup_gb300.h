@@ -158,6 +158,18 @@ cup_status cup_rref(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64
                     int64_t *d_profile, int64_t *rank, uint32_t *X, int64_t ldx, void *stream);
 
 /*
+ * Basis of the right nullspace {x : A x = 0} (the echelon transform of Sec. 3.4
+ * and 3.5 gives it, Sec. 4.4): with A X = R for the transform X of cup_rref,
+ * R's columns r .. n-1 are zero, so X's columns r .. n-1 are a basis. A (m x n)
+ * is destroyed (it holds the CUP factors and the echelon work). Nb is a
+ * caller-owned n x ldn device matrix, ldn >= n: on success its first n - r
+ * columns hold the basis P^T [X2; I_{n-r}] (its other columns are untouched)
+ * and *rank = r. n - r = 0 writes nothing.
+ */
+cup_status cup_nullspace(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                         uint32_t *Nb, int64_t ldn, int64_t *rank, void *stream);
+
+/*
  * Linear system A X = B (Sec. 4.4: solving reduces to CUP). A (m x n) is
  * destroyed; B (m x k, ldb) is read and destroyed; X (n x k, ldx) receives
  * the solution whose entries outside the CUP pivot columns are zero

@@ -206,6 +206,15 @@ def rref(A, p: int, want_x: bool = False):
     return dict(rank=int(r), profile=prof[:r].copy(), R=R, X=X)
 
 
+def nullspace(A, p: int):
+    """Basis of the right nullspace {x : A x = 0}: with A X = R (the reduced column
+    echelon transform of `rref`), R's columns r .. n-1 vanish, so X's columns r .. n-1
+    are a basis (Sec. 3.4, 3.5 and 4.4). Returns dict(rank, N) with N of shape (n, n - r)."""
+    d = rref(A, p, want_x=True)
+    r = d["rank"]
+    return dict(rank=r, N=np.ascontiguousarray(d["X"][:, r:]))
+
+
 def det(A, p: int) -> int:
     """Determinant by row-echelon elimination with interchanges."""
     A = _u32arr(A)

@@ -60,6 +60,7 @@ SIGNATURES = {
     "cup_inverse": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
     "cup_rref": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P, _I64, _P]),
     "cup_solve": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P, _I64, _U32, _I64P, _P]),
+    "cup_nullspace": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64, _I64P, _P]),
     "cup_mm_sub": (_INT, [_P, _P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _INT, _P]),
     "cup_trsm_ruu": (_INT, [_P, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
     "cup_laswp_cols": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P]),
@@ -242,6 +243,17 @@ class Handle:
         self._check(st, "cup_rref", self.h)
         return r.value, prof[: r.value], X
 
+    def nullspace(self, A, p: int, stream=None):
+        """Basis of {x : A x = 0} (A is destroyed); returns (rank, N) with N of shape (n, n - rank)."""
+        torch = _torch()
+        m, n, lda = _mat(A, "A")
+        Nb = torch.empty((max(n, 1), max(n, 1)), dtype=torch.int32, device=A.device)
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_nullspace(self.h, A.data_ptr(), m, n, lda, p, Nb.data_ptr(), max(n, 1),
+                                    ctypes.byref(r), _stream_ptr(stream))
+        self._check(st, "cup_nullspace", self.h)
+        return r.value, Nb[:n, : n - r.value]
+
     def solve(self, A, B, p: int, stream=None):
         """Solve A X = B; returns (status, X, rank) with status 0 or 2 (inconsistent)."""
         torch = _torch()
@@ -386,6 +398,10 @@ def rref(A, p, want_x=False, engine=None, stream=None):
 
 def solve(A, B, p, engine=None, stream=None):
     return _handle(engine).solve(A, B, p, stream)
+
+
+def nullspace(A, p, engine=None, stream=None):
+    return _handle(engine).nullspace(A, p, stream)
 
 
 def mm_sub(C, A, B, p, engine=ENGINE_TENSOR, stream=None):

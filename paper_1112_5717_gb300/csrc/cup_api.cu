@@ -1126,6 +1126,47 @@ cup_status cup_rref(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t ld
     return s;
 }
 
+cup_status cup_nullspace(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                         uint32_t *Nb, int64_t ldn, int64_t *rank, void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1) || ldn < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    if (n == 0) return CUP_OK;
+    if (!Nb) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (m == 0) {
+        // every vector is in the nullspace: the identity
+        CU(launch_fill(Nb, ldn, n, n, 1, st));
+        CU(cudaStreamSynchronize(st));
+        return CUP_OK;
+    }
+    if (!A) return CUP_ERR_ARG;
+    const int64_t kmn = m < n ? m : n;
+    int64_t *d_ipiv = nullptr, *d_prof = nullptr;
+    CU(cudaMalloc(&d_ipiv, (size_t)kmn * sizeof(int64_t)));
+    if (cudaMalloc(&d_prof, (size_t)kmn * sizeof(int64_t)) != cudaSuccess) {
+        cudaFree(d_ipiv);
+        return CUP_ERR_NOMEM;
+    }
+    int64_t r = 0;
+    const ModP M = make_modp(p);
+    cup_status s = cup_factor(h, A, m, n, lda, p, d_prof, d_ipiv, &r, stream);
+    if (s == CUP_OK) s = red_col_ech(h, A, m, n, lda, r, d_prof, M, h->engine, st);
+    if (s == CUP_OK && r < n) {
+        // columns r .. n-1 of X = P^T [X1 X2; 0 I]: P^T [X2; I_{n-r}]
+        s = cuda_ok(h, launch_copy(Nb, ldn, A + r, lda, r, n - r, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_fill(Nb + r * ldn, ldn, n - r, n - r, 1, st));
+        if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(Nb, ldn, n - r, d_ipiv, r, 0, 0, 1, 0, st));
+    }
+    if (s == CUP_OK) s = check_device_error(h, st);
+    if (s == CUP_OK) *rank = r;
+    cudaFree(d_ipiv);
+    cudaFree(d_prof);
+    return s;
+}
+
 cup_status cup_solve(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t *B,
                      int64_t k, int64_t ldb, uint32_t *X, int64_t ldx, uint32_t p, int64_t *rank,
                      void *stream)

@@ -179,3 +179,21 @@ def test_rank_profile(handle, m, n, p):
     r, prof = handle.rank_profile(_dev(A), p)
     assert r == want["rank"]
     assert np.array_equal(prof.cpu().numpy(), want["profile"])
+
+
+@pytest.mark.parametrize("m,n,r,p", [(40, 60, 25, 65521), (64, 64, 64, 8388593), (100, 37, 20, 251),
+                                     (30, 90, 0, 7), (130, 200, 120, 2147483647), (1, 5, 1, 2)])
+def test_nullspace(handle, m, n, r, p):
+    """cup_nullspace equals the oracle's basis (the last n - r columns of the echelon
+    transform) bit for bit, and the basis is annihilated by A."""
+    rng = np.random.default_rng(3 * m + n + r)
+    A = np.zeros((m, n), dtype=np.int64) if r == 0 else (
+        low_rank(rng, m, n, r, p) if r < min(m, n) else rng.integers(0, p, size=(m, n)))
+    want = oracle.nullspace(A, p)
+    rank, N = handle.nullspace(_dev(A), p)
+    assert rank == want["rank"] == r
+    got = _host(N.contiguous())
+    assert got.shape == (n, n - r)
+    assert np.array_equal(got, want["N"].astype(np.int64))
+    if n - r:
+        assert not exact_matmul_mod(A, got, p).any()

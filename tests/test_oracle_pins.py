@@ -387,3 +387,24 @@ def test_workload_generators_structure():
     for b, (Ab, pb) in enumerate(mats):
         assert Ab.shape == (m[b], n[b]) and pb == primes[b % 64]
         assert oracle.cup(Ab, pb)["rank"] == r[b]
+
+
+@pytest.mark.parametrize("m,n,r,p", [(5, 7, 3, 13), (20, 12, 12, 65521), (12, 20, 7, 251), (9, 9, 0, 7),
+                                     (30, 30, 30, 2147483647), (6, 15, 2, 2)])
+def test_oracle_nullspace_spans_the_kernel(m, n, r, p):
+    """A N = 0 mod p, N has full column rank n - r (checked by the oracle's own
+    elimination of N^T), and the sizes add up (rank-nullity); the zero matrix gives
+    the identity."""
+    from tests._helpers import exact_matmul_mod, low_rank
+    rng = np.random.default_rng(m * 100 + n + r)
+    A = np.zeros((m, n), dtype=np.int64) if r == 0 else (
+        low_rank(rng, m, n, r, p) if r < min(m, n) else rng.integers(0, p, size=(m, n)))
+    d = oracle.nullspace(A, p)
+    N = d["N"].astype(np.int64)
+    assert d["rank"] == r
+    assert N.shape == (n, n - r)
+    if n - r:
+        assert not exact_matmul_mod(A, N, p).any()
+        assert oracle.cup(N.T.copy(), p)["rank"] == n - r
+    if r == 0:
+        assert np.array_equal(N, np.eye(n, dtype=np.int64))
