@@ -158,6 +158,21 @@ cup_status cup_rref(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64
                     int64_t *d_profile, int64_t *rank, uint32_t *X, int64_t ldx, void *stream);
 
 /*
+ * PLE decomposition (Sec. 5, Algorithm 10): the row echelon twin of CUP. A (m x n)
+ * is overwritten by [L\E] such that A = P L E, where E (r x n, rows 0 .. r-1 of A,
+ * on and right of each row's first nonzero) is in row echelon form revealing the
+ * column rank profile, L (m x r, strictly below the diagonal of A's first r
+ * columns) is unit lower triangular, and P is a row permutation stored as
+ * transpositions: exchanging rows t and d_ipiv[t] of the input, in order
+ * t = 0 .. r-1, gives L E (so A = P L E). d_profile receives the column rank
+ * profile. (E^T, L^T, P^T) is the CUP decomposition of
+ * A^T that cup_factor computes, and this is how it is computed: CUP of a
+ * transposed copy (m n uint32 of scratch owned by the call), transposed back.
+ */
+cup_status cup_ple(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                   int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, void *stream);
+
+/*
  * Basis of the right nullspace {x : A x = 0} (the echelon transform of Sec. 3.4
  * and 3.5 gives it, Sec. 4.4): with A X = R for the transform X of cup_rref,
  * R's columns r .. n-1 are zero, so X's columns r .. n-1 are a basis. A (m x n)

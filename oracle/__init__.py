@@ -206,6 +206,16 @@ def rref(A, p: int, want_x: bool = False):
     return dict(rank=int(r), profile=prof[:r].copy(), R=R, X=X)
 
 
+def ple(A, p: int):
+    """PLE decomposition (Sec. 5): (E^T, L^T, P^T) is the CUP decomposition of A^T,
+    so this is `cup_packed` of A^T, transposed. Returns dict(rank, profile (the column
+    rank profile), ipiv (row exchanges), packed = [L\\E] as an m x n array)."""
+    A = _u32arr(A)
+    d = cup_packed(np.ascontiguousarray(A.T), p)
+    return dict(rank=d["rank"], profile=d["profile"], ipiv=d["ipiv"],
+                packed=np.ascontiguousarray(d["packed"].T))
+
+
 def nullspace(A, p: int):
     """Basis of the right nullspace {x : A x = 0}: with A X = R (the reduced column
     echelon transform of `rref`), R's columns r .. n-1 vanish, so X's columns r .. n-1

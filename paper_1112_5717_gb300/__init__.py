@@ -61,6 +61,7 @@ SIGNATURES = {
     "cup_rref": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P, _I64, _P]),
     "cup_solve": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P, _I64, _U32, _I64P, _P]),
     "cup_nullspace": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64, _I64P, _P]),
+    "cup_ple": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_mm_sub": (_INT, [_P, _P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _INT, _P]),
     "cup_trsm_ruu": (_INT, [_P, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
     "cup_laswp_cols": (_INT, [_P, _P, _I64, _I64, _I64, _P, _I64, _I64, _P]),
@@ -243,6 +244,19 @@ class Handle:
         self._check(st, "cup_rref", self.h)
         return r.value, prof[: r.value], X
 
+    def ple(self, A, p: int, stream=None):
+        """A <- [L\\E] with A = P L E (row echelon twin of CUP); returns (rank, column profile, ipiv)."""
+        torch = _torch()
+        m, n, lda = _mat(A, "A")
+        k = max(min(m, n), 1)
+        prof = torch.empty(k, dtype=torch.int64, device=A.device)
+        ipiv = torch.empty(k, dtype=torch.int64, device=A.device)
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_ple(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(), ipiv.data_ptr(),
+                              ctypes.byref(r), _stream_ptr(stream))
+        self._check(st, "cup_ple", self.h)
+        return r.value, prof[: r.value], ipiv[: r.value]
+
     def nullspace(self, A, p: int, stream=None):
         """Basis of {x : A x = 0} (A is destroyed); returns (rank, N) with N of shape (n, n - rank)."""
         torch = _torch()
@@ -398,6 +412,10 @@ def rref(A, p, want_x=False, engine=None, stream=None):
 
 def solve(A, B, p, engine=None, stream=None):
     return _handle(engine).solve(A, B, p, stream)
+
+
+def ple(A, p, engine=None, stream=None):
+    return _handle(engine).ple(A, p, stream)
 
 
 def nullspace(A, p, engine=None, stream=None):

@@ -1126,6 +1126,28 @@ cup_status cup_rref(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t ld
     return s;
 }
 
+cup_status cup_ple(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p, int64_t *d_profile,
+                   int64_t *d_ipiv, int64_t *rank, void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!A || !d_profile || !d_ipiv) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *T = nullptr;
+    CU(cudaMalloc(&T, (size_t)m * (size_t)n * sizeof(uint32_t)));
+    int64_t r = 0;
+    cup_status s = cuda_ok(h, launch_transpose(T, m, A, lda, m, n, st));          // T = A^T (n x m)
+    if (s == CUP_OK) s = cup_factor(h, T, n, m, m, p, d_profile, d_ipiv, &r, stream);
+    if (s == CUP_OK) s = cuda_ok(h, launch_transpose(A, lda, T, m, n, m, st));   // [L\E] = [C\U]^T
+    if (s == CUP_OK) s = cuda_ok(h, cudaStreamSynchronize(st));
+    if (s == CUP_OK) *rank = r;
+    cudaFree(T);
+    return s;
+}
+
 cup_status cup_nullspace(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
                          uint32_t *Nb, int64_t ldn, int64_t *rank, void *stream)
 {

@@ -155,6 +155,8 @@ cudaError_t launch_gather_rows(uint32_t *dst, int64_t ldd, const uint32_t *src, 
                                int64_t nrows, int64_t ncols, cudaStream_t st);
 cudaError_t launch_fill(uint32_t *B, int64_t ldb, int64_t m, int64_t n, int diag, cudaStream_t st);
 cudaError_t launch_any_nonzero(const uint32_t *B, int64_t ldb, int64_t m, int64_t n, int *flag, cudaStream_t st);
+cudaError_t launch_transpose(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
+                             cudaStream_t st);
 cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
                         cudaStream_t st);
 cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t st);

@@ -520,6 +520,38 @@ cudaError_t launch_any_nonzero(const uint32_t *B, int64_t ldb, int64_t m, int64_
     return cudaGetLastError();
 }
 
+// D (n x m) <- S^T for an m x n block S: 32 x 32 tiles through shared memory, so
+// that both the reads and the writes run along rows.
+__global__ void __launch_bounds__(256)
+k_transpose(uint32_t *__restrict__ D, int64_t ldd, const uint32_t *__restrict__ S, int64_t lds, int64_t m,
+            int64_t n)
+{
+    __shared__ uint32_t t[32][33];
+    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;       // 8 rows of 32
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = i0 + ty + 8 * k, j = j0 + tx;
+        if (i < m && j < n) t[ty + 8 * k][tx] = S[i * lds + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t j = j0 + ty + 8 * k, i = i0 + tx;           // D row j, column i
+        if (j < n && i < m) D[j * ldd + i] = t[tx][ty + 8 * k];
+    }
+}
+
+cudaError_t launch_transpose(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
+                             cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if ((n + 31) / 32 > 0x7fffffff || (m + 31) / 32 > 65535) return cudaErrorInvalidValue;
+    dim3 g((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+    k_transpose<<<g, 256, 0, st>>>(D, ldd, S, lds, m, n);
+    return cudaGetLastError();
+}
+
 // Copy an m x n block (non-overlapping).
 __global__ void k_copy(uint32_t *__restrict__ D, int64_t ldd, const uint32_t *__restrict__ S, int64_t lds,
                        int64_t m, int64_t n)

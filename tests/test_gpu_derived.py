@@ -197,3 +197,20 @@ def test_nullspace(handle, m, n, r, p):
     assert np.array_equal(got, want["N"].astype(np.int64))
     if n - r:
         assert not exact_matmul_mod(A, got, p).any()
+
+
+@pytest.mark.parametrize("m,n,r,p", [(50, 70, 30, 65521), (70, 50, 50, 8388593), (129, 200, 129, 251),
+                                     (300, 100, 60, 2147483647), (64, 64, 0, 7), (1, 9, 1, 2)])
+def test_ple(handle, m, n, r, p):
+    """cup_ple equals the oracle's PLE bit for bit: [L\\E], the column rank profile and
+    the row exchanges."""
+    rng = np.random.default_rng(5 * m + n + r)
+    A = np.zeros((m, n), dtype=np.int64) if r == 0 else (
+        low_rank(rng, m, n, r, p) if r < min(m, n) else rng.integers(0, p, size=(m, n)))
+    want = oracle.ple(A, p)
+    dA = _dev(A)
+    rank, prof, ipiv = handle.ple(dA, p)
+    assert rank == want["rank"] == r
+    assert np.array_equal(prof.cpu().numpy(), want["profile"])
+    assert np.array_equal(ipiv.cpu().numpy(), want["ipiv"])
+    assert np.array_equal(_host(dA), want["packed"].astype(np.int64))

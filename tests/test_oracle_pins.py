@@ -408,3 +408,38 @@ def test_oracle_nullspace_spans_the_kernel(m, n, r, p):
         assert oracle.cup(N.T.copy(), p)["rank"] == n - r
     if r == 0:
         assert np.array_equal(N, np.eye(n, dtype=np.int64))
+
+
+def _ple_parts(packed, r):
+    m, n = packed.shape
+    P = packed.astype(np.int64)
+    L = np.zeros((m, r), dtype=np.int64)
+    for t in range(r):
+        L[t, t] = 1
+        L[t + 1:, t] = P[t + 1:, t]
+    E = np.triu(P[:r, :])
+    return L, E
+
+
+@pytest.mark.parametrize("m,n,r,p", [(6, 5, 3, 3), (5, 6, 4, 2), (12, 9, 9, 65521), (9, 12, 5, 251),
+                                     (40, 30, 17, 2147483647)])
+def test_oracle_ple_reconstructs_and_reveals_the_column_profile(m, n, r, p):
+    """Exchanging rows t and ipiv[t] in order gives L E; L is unit lower, E is in row
+    echelon form whose leading columns are the profile; the profile is the column
+    rank profile by definition (spans of earlier columns, exhaustive for tiny p)."""
+    from tests._helpers import exact_matmul_mod, low_rank, span_profile
+    rng = np.random.default_rng(m + 10 * n + r)
+    A = low_rank(rng, m, n, r, p) if r < min(m, n) else rng.integers(0, p, size=(m, n))
+    d = oracle.ple(A, p)
+    rr = d["rank"]
+    assert rr == r
+    L, E = _ple_parts(d["packed"], rr)
+    PA = np.asarray(A, dtype=np.int64).copy()
+    for t, c in enumerate(d["ipiv"]):
+        PA[[t, c]] = PA[[c, t]]
+    assert np.array_equal(exact_matmul_mod(L, E, p), PA % p)
+    lead = [int(np.flatnonzero(E[t])[0]) for t in range(rr)]
+    assert lead == list(d["profile"])
+    assert all(a < b for a, b in zip(lead, lead[1:]))
+    if p ** min(m, n) <= 4096:
+        assert lead == span_profile(np.asarray(A).T, p)
