@@ -52,6 +52,9 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)
     ap.add_argument("--engine", choices=["tensor", "plain"], default="tensor")
+    ap.add_argument("--op", choices=list(OPS), default="factor",
+                    help="operation timed on the workload: factor (CUP, the headline), ple, det, inverse, rref, "
+                         "nullspace; inverse, rref and nullspace need a square nonsingular workload")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-engine comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -193,7 +196,60 @@ def make_workload(args):
 # ---------------------------------------------------------------------------
 # the CPU oracle as baseline (test infrastructure, timed as it stands)
 # ---------------------------------------------------------------------------
-def oracle_sample(n: int, p: int, workload: str = "dense_full"):
+# Operations and their leading-term operation counts (Table 1, omega = 3): CUP, PLE and
+# det cost 2mnr - (m+n) r^2 + 2/3 r^3; the reduced echelon transform (inverse, rref,
+# nullspace) of a nonsingular n x n matrix costs 2 n^3.
+OPS = ("factor", "ple", "det", "inverse", "rref", "nullspace")
+
+
+def op_ops(op: str, m: int, n: int, r: int) -> float:
+    if op in ("factor", "ple", "det"):
+        return cup_ops(m, n, r)
+    if m != n or r != n:
+        raise SystemExit(f"--op {op} needs a square nonsingular workload")
+    return 2.0 * float(n) ** 3
+
+
+def op_metric(op: str) -> str:
+    return METRIC if op == "factor" else f"{op} over GF(p) Gop/s (Table 1 leading term)"
+
+
+def run_op(h, op: str, A, p: int):
+    """One call of the operation through the library; returns the rank."""
+    if op == "factor":
+        return h.factor(A, p)[0]
+    if op == "ple":
+        return h.ple(A, p)[0]
+    if op == "det":
+        h.det(A, p)
+        return min(A.shape)
+    if op == "inverse":
+        h.inverse(A, p)
+        return A.shape[0]
+    if op == "rref":
+        return h.rref(A, p)[0]
+    return h.nullspace(A, p)[0]
+
+
+def oracle_op(op: str, A, p: int):
+    """The oracle's version of the operation; returns the rank."""
+    import oracle
+    if op == "factor":
+        return oracle.cup(A, p)["rank"]
+    if op == "ple":
+        return oracle.ple(A, p)["rank"]
+    if op == "det":
+        oracle.det(A, p)
+        return min(A.shape)
+    if op == "inverse":
+        oracle.inverse(A, p)
+        return A.shape[0]
+    if op == "rref":
+        return oracle.rref(A, p, want_x=True)["rank"]
+    return oracle.nullspace(A, p)["rank"]
+
+
+def oracle_sample(n: int, p: int, workload: str = "dense_full", op: str = "factor"):
     """Times the oracle on one bounded sample of the workload; returns
     (Gop/s, seconds, threads, description)."""
     import oracle
@@ -210,11 +266,13 @@ def oracle_sample(n: int, p: int, workload: str = "dense_full"):
     else:
         mats = [(inputs.dense_full(n=n, p=p, seed=inputs.SEED_BASE + 2), p)]
         desc = f"CUP of one {n}x{n} uniform matrix over GF({p}) (the workload scaled down)"
+    if op != "factor":
+        desc = desc.replace("CUP", op, 1)
     t0 = time.perf_counter()
     ops = 0.0
     for A, q in mats:
-        d = oracle.cup(A, q)
-        ops += cup_ops(A.shape[0], A.shape[1], d["rank"])
+        rr = oracle_op(op, A, q)
+        ops += op_ops(op, A.shape[0], A.shape[1], rr)
     dt = time.perf_counter() - t0
     return ops / dt / 1e9, dt, oracle.num_threads(), desc
 
@@ -228,15 +286,15 @@ def run_reference(args):
     n = args.cpu_sample
     p = args.p or 65521
     for _ in range(args.warmup):
-        oracle_sample(n, p, args.workload)
+        oracle_sample(n, p, args.workload, args.op)
     vals, times = [], []
     for _ in range(args.steps):
-        v, dt, cores, desc = oracle_sample(n, p, args.workload)
+        v, dt, cores, desc = oracle_sample(n, p, args.workload, args.op)
         vals.append(v)
         times.append(dt)
     value = statistics.median(vals)
     sample = f"{desc}, per step; leading-term ops / wall time"
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    out = {"impl": "reference", "metric": op_metric(args.op), "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(times) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
            "data": "synthetic",
@@ -285,12 +343,14 @@ def run_ours(args):
         for w_, p_ in zip(work, pristine):
             w_.copy_(p_)
 
+    if batched and args.op != "factor":
+        raise SystemExit("the batched workload times the factorization only")
+
     def compute():
         if batched:
             ranks, _, _, _ = h.factor_batched(work, primes)
             return ranks
-        r, _, _ = h.factor(work[0], primes[0])
-        return r
+        return run_op(h, args.op, work[0], primes[0])
 
     def one_step():
         restore()
@@ -307,7 +367,7 @@ def run_ours(args):
         ranks_v = out.cpu().numpy().tolist()
     else:
         ranks_v = [out]
-    ops = sum(cup_ops(A.shape[0], A.shape[1], rr) for (A, _), rr in zip(mats, ranks_v))
+    ops = sum(op_ops(args.op, A.shape[0], A.shape[1], rr) for (A, _), rr in zip(mats, ranks_v))
     h.reset_stats()
     clocks = ClockSampler(dev)
     clocks.start()
@@ -341,11 +401,13 @@ def run_ours(args):
     value = ops * world / (ms_max * 1e-3) / 1e9
     shape = {"matrices": len(mats)} if batched else {"m": mats[0][0].shape[0], "n": mats[0][0].shape[1],
                                                      "p": primes[0], "rank": ranks_v[0]}
-    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    result = {"metric": op_metric(args.op), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "u32", "data": "synthetic",
               "config": dict({"workload": wname + (" (one persistent launch)" if batched else
-                                                   f", in-place CUP (Algorithm 6), {args.engine} Schur updates"),
+                                                   (f", in-place CUP (Algorithm 6), {args.engine} Schur updates" if args.op == "factor" else
+                                                    f", {args.op} through the library (CUP, Algorithms 7-8 or Sec. 5), "
+                                                    f"{args.engine} Schur updates")),
                               "engine": args.engine, "leading_term_ops": ops,
                               "limbs": cup_limbs(primes[0]) if engine == cup.ENGINE_TENSOR else None,
                               "l2": "inputs restored by a device copy before each step; "
@@ -415,13 +477,13 @@ def run_ours(args):
     if not args.no_plain and engine == cup.ENGINE_TENSOR and world == 1 and not batched:
         hp = cup.Handle(dev, engine=cup.ENGINE_PLAIN, **opts)
         restore()
-        hp.factor(work[0], primes[0])
+        run_op(hp, args.op, work[0], primes[0])
         pm = []
         for _ in range(2):
             restore()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            hp.factor(work[0], primes[0])
+            run_op(hp, args.op, work[0], primes[0])
             e1.record(stream)
             torch.cuda.synchronize()
             pm.append(e0.elapsed_time(e1))
@@ -431,7 +493,8 @@ def run_ours(args):
         hp.close()
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, cores, desc = oracle_sample(args.cpu_sample, primes[0] if not batched else 0, args.workload)
+        v, dt, cores, desc = oracle_sample(args.cpu_sample, primes[0] if not batched else 0, args.workload,
+                                           args.op)
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": f"{desc} ({dt:.1f} s), leading-term ops / wall time"}
     if rank == 0:
