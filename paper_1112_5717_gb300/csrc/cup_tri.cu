@@ -49,7 +49,7 @@ __device__ void load_tri(const uint32_t *T, int64_t ldt, int n, const ModP &M,
         uint32_t d = 1u % M.p;
         if (!UNIT && k < n) {
             d = T[k * ldt + k];
-            if (SOLVE) d = invm(d, M);
+            if (SOLVE) d = MONT ? invm_mont(d, M) : invm(d, M);
         }
         sD[k] = to_mont<MONT>(d, M);
     }
@@ -108,47 +108,84 @@ k_tri_right(const TriDesc d, ModP M)
     }
 }
 
-#define TRI_COLS 64
+// B <- T^{-1} B or B <- T B for n <= 64 rows of B: a CTA takes 32 columns, loads the
+// 64 x 32 tile row by row (coalesced) into shared memory, and each warp works on four
+// columns at once with the lanes along the rows (rows lane and lane + 32): a solve
+// finalises row i, broadcasts it from its lane and the dependent rows subtract
+// t_ki x_i (four independent chains per warp); a product needs no chain.
+#define TRI_COLS 32
 template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
-__global__ void __launch_bounds__(TRI_COLS)
+__global__ void __launch_bounds__(256)
 k_tri_left(const uint32_t *__restrict__ T, int64_t ldt, uint32_t *__restrict__ B, int64_t ldb, int n,
            int64_t k, ModP M)
 {
     __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
     __shared__ uint32_t sD[TRI_MAX];
-    __shared__ uint32_t sB[TRI_MAX][TRI_COLS];
+    __shared__ uint32_t sB[TRI_MAX][TRI_COLS + 1];
     load_tri<UPPER, UNIT, SOLVE, MONT>(T, ldt, n, M, sT, sD);
-    const int c = threadIdx.x;
-    const int64_t col = (int64_t)blockIdx.x * TRI_COLS + c;
-    for (int i = 0; i < n; ++i) sB[i][c] = (col < k) ? B[i * ldb + col] : 0u;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t c0 = (int64_t)blockIdx.x * TRI_COLS;
+    for (int i = warp; i < n; i += 8) sB[i][lane] = (c0 + lane < k) ? B[i * ldb + c0 + lane] : 0u;
     __syncthreads();
-    if (col >= k) return;
+    // warp w: columns w, w + 8, w + 16, w + 24 of the tile
+    uint32_t x[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = warp + 8 * q;
+        x[q][0] = (lane < n) ? sB[lane][c] : 0u;
+        x[q][1] = (lane + 32 < n) ? sB[lane + 32][c] : 0u;
+    }
     if (SOLVE) {
-        // T X = B: rows in dependency order
         for (int s = 0; s < n; ++s) {
             const int i = UPPER ? n - 1 - s : s;
-            uint32_t acc = sB[i][c];
-            if (UPPER) {
-                for (int j = i + 1; j < n; ++j) acc = subm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
-            } else {
-                for (int j = 0; j < i; ++j) acc = subm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
+            const int hi = i >> 5, li = i & 31;
+            // the row's value is final once its diagonal is divided out
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!UNIT && lane == li) x[q][hi] = mmul<MONT>(x[q][hi], sD[i], M);
             }
-            sB[i][c] = mmul<MONT>(acc, sD[i], M);
+            const uint32_t t0 = sT[lane][i], t1 = sT[lane + 32][i];
+            const bool d0 = UPPER ? lane < i : lane > i, d1 = UPPER ? lane + 32 < i : lane + 32 > i;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t xi = __shfl_sync(0xffffffffu, hi ? x[q][1] : x[q][0], li);
+                if (xi) {
+                    if (d0) x[q][0] = subm(x[q][0], mmul<MONT>(xi, t0, M), M);
+                    if (d1) x[q][1] = subm(x[q][1], mmul<MONT>(xi, t1, M), M);
+                }
+            }
         }
     } else {
-        // Y = T B; rows are overwritten in an order that keeps the inputs they need
-        for (int s = 0; s < n; ++s) {
-            const int i = UPPER ? s : n - 1 - s;
-            uint32_t acc = mmul<MONT>(sB[i][c], sD[i], M);
-            if (UPPER) {
-                for (int j = i + 1; j < n; ++j) acc = addm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
-            } else {
-                for (int j = 0; j < i; ++j) acc = addm(acc, mmul<MONT>(sB[j][c], sT[i][j], M), M);
-            }
-            sB[i][c] = acc;
+        // Y = T B: y_i = d_i x_i + sum over the triangle of t_ij x_j
+        uint32_t y[4][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            y[q][0] = mmul<MONT>(x[q][0], sD[lane], M);
+            y[q][1] = mmul<MONT>(x[q][1], sD[lane + 32], M);
         }
+        for (int j = 0; j < n; ++j) {
+            const int hj = j >> 5, lj = j & 31;
+            const uint32_t t0 = sT[lane][j], t1 = sT[lane + 32][j];
+            const bool d0 = UPPER ? lane < j : lane > j, d1 = UPPER ? lane + 32 < j : lane + 32 > j;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t xj = __shfl_sync(0xffffffffu, hj ? x[q][1] : x[q][0], lj);
+                if (d0) y[q][0] = addm(y[q][0], mmul<MONT>(xj, t0, M), M);
+                if (d1) y[q][1] = addm(y[q][1], mmul<MONT>(xj, t1, M), M);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { x[q][0] = y[q][0]; x[q][1] = y[q][1]; }
     }
-    for (int i = 0; i < n; ++i) B[i * ldb + col] = sB[i][c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = warp + 8 * q;
+        if (lane < n) sB[lane][c] = x[q][0];
+        if (lane + 32 < n) sB[lane + 32][c] = x[q][1];
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += 8)
+        if (c0 + lane < k) B[i * ldb + c0 + lane] = sB[i][lane];
 }
 
 template <bool UPPER, bool UNIT, bool SOLVE>
@@ -158,8 +195,8 @@ static cudaError_t tri_dispatch(bool left, const uint32_t *T, int64_t ldt, uint3
     const bool mont = (M.p & 1u) != 0;
     if (left) {
         const int64_t nb = (cols + TRI_COLS - 1) / TRI_COLS;
-        if (mont) k_tri_left<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, TRI_COLS, 0, st>>>(T, ldt, B, ldb, n, cols, M);
-        else k_tri_left<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, TRI_COLS, 0, st>>>(T, ldt, B, ldb, n, cols, M);
+        if (mont) k_tri_left<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, n, cols, M);
+        else k_tri_left<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, n, cols, M);
     } else {
         int64_t nb = (rows + 7) / 8;
         if (nb > 152 * 16) nb = 152 * 16;
@@ -579,33 +616,49 @@ cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds
 // triangular block, one thread per column j solving T x = e_j.
 // ---------------------------------------------------------------------------
 template <bool UPPER, bool UNIT, bool MONT>
-__global__ void __launch_bounds__(TRI_MAX)
+__global__ void __launch_bounds__(512)
 k_trtri_leaf(uint32_t *__restrict__ T, int64_t ldt, int n, ModP M)
 {
+    // T^{-1} as the solution of T X = I: sixteen warps, four columns each, lanes along
+    // the rows; row i is finalised (divided by its diagonal), broadcast from its lane,
+    // and the rows that depend on it subtract t_ki x_i
     __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
     __shared__ uint32_t sD[TRI_MAX];
     __shared__ uint32_t sX[TRI_MAX][TRI_MAX + 1];
     load_tri<UPPER, UNIT, true, MONT>(T, ldt, n, M, sT, sD);
     __syncthreads();
-    const int j = threadIdx.x;
-    if (j < n) {
-        if (UPPER) {
-            sX[j][j] = MONT ? redc((uint64_t)sD[j], M) : sD[j];       // plain 1 / U[j][j]
-            for (int i = j - 1; i >= 0; --i) {
-                uint32_t acc = 0u;
-                for (int k = i + 1; k <= j; ++k) acc = addm(acc, mmul<MONT>(sX[k][j], sT[i][k], M), M);
-                const uint32_t v = mmul<MONT>(acc, sD[i], M);
-                sX[i][j] = v ? M.p - v : 0u;
-            }
-        } else {
-            sX[j][j] = MONT ? redc((uint64_t)sD[j], M) : sD[j];
-            for (int i = j + 1; i < n; ++i) {
-                uint32_t acc = 0u;
-                for (int k = j; k < i; ++k) acc = addm(acc, mmul<MONT>(sX[k][j], sT[i][k], M), M);
-                const uint32_t v = mmul<MONT>(acc, sD[i], M);
-                sX[i][j] = v ? M.p - v : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t one = 1u % M.p;
+    uint32_t x[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = warp + 16 * q;
+        x[q][0] = (lane == c) ? one : 0u;
+        x[q][1] = (lane + 32 == c) ? one : 0u;
+    }
+    for (int s = 0; s < n; ++s) {
+        const int i = UPPER ? n - 1 - s : s;
+        const int hi = i >> 5, li = i & 31;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!UNIT && lane == li) x[q][hi] = mmul<MONT>(x[q][hi], sD[i], M);
+        }
+        const uint32_t t0 = sT[lane][i], t1 = sT[lane + 32][i];
+        const bool d0 = UPPER ? lane < i : lane > i, d1 = UPPER ? lane + 32 < i : lane + 32 > i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t xi = __shfl_sync(0xffffffffu, hi ? x[q][1] : x[q][0], li);
+            if (xi) {
+                if (d0) x[q][0] = subm(x[q][0], mmul<MONT>(xi, t0, M), M);
+                if (d1) x[q][1] = subm(x[q][1], mmul<MONT>(xi, t1, M), M);
             }
         }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = warp + 16 * q;
+        sX[lane][c] = x[q][0];
+        sX[lane + 32][c] = x[q][1];
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -621,8 +674,8 @@ cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int
     if (n > TRI_MAX) return cudaErrorInvalidValue;
     const bool mont = (M.p & 1u) != 0;
 #define TRTRI_CASE(U, D)                                                                     \
-    if (mont) k_trtri_leaf<U, D, true><<<1, TRI_MAX, 0, st>>>(T, ldt, n, M);                 \
-    else k_trtri_leaf<U, D, false><<<1, TRI_MAX, 0, st>>>(T, ldt, n, M);
+    if (mont) k_trtri_leaf<U, D, true><<<1, 512, 0, st>>>(T, ldt, n, M);                     \
+    else k_trtri_leaf<U, D, false><<<1, 512, 0, st>>>(T, ldt, n, M);
     if (upper && unit) { TRTRI_CASE(true, true) }
     else if (upper) { TRTRI_CASE(true, false) }
     else if (unit) { TRTRI_CASE(false, true) }
