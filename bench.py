@@ -199,7 +199,7 @@ def make_workload(args):
 # Operations and their leading-term operation counts (Table 1, omega = 3): CUP, PLE and
 # det cost 2mnr - (m+n) r^2 + 2/3 r^3; the reduced echelon transform (inverse, rref,
 # nullspace) of a nonsingular n x n matrix costs 2 n^3.
-OPS = ("factor", "ple", "det", "inverse", "rref", "nullspace")
+OPS = ("factor", "ple", "det", "inverse", "rref", "nullspace", "trlum", "inplace_mm")
 
 
 def op_ops(op: str, m: int, n: int, r: int) -> float:
@@ -207,6 +207,11 @@ def op_ops(op: str, m: int, n: int, r: int) -> float:
         return cup_ops(m, n, r)
     if m != n or r != n:
         raise SystemExit(f"--op {op} needs a square nonsingular workload")
+    if op == "trlum":
+        return 2.0 / 3.0 * float(n) ** 3
+    if op == "inplace_mm":
+        # CUP + TRMM(Up, Unit) + TRMM(Low) + TRLUM with B = A (n x n): (2/3 + 2 + 2/3) n^3
+        return 10.0 / 3.0 * float(n) ** 3
     return 2.0 * float(n) ** 3
 
 
@@ -228,7 +233,25 @@ def run_op(h, op: str, A, p: int):
         return A.shape[0]
     if op == "rref":
         return h.rref(A, p)[0]
+    if op == "trlum":
+        h.trlum(A, p)
+        return A.shape[0]
+    if op == "inplace_mm":
+        # B <- A B with B a device copy of A, made inside the call
+        B = _op_scratch(A)
+        B.copy_(A)
+        return h.inplace_mm(A, B, p)
     return h.nullspace(A, p)[0]
+
+
+_SCRATCH = {}
+
+
+def _op_scratch(A):
+    key = (tuple(A.shape), A.device)
+    if key not in _SCRATCH:
+        _SCRATCH[key] = A.clone()
+    return _SCRATCH[key]
 
 
 def oracle_op(op: str, A, p: int):
@@ -246,6 +269,12 @@ def oracle_op(op: str, A, p: int):
         return A.shape[0]
     if op == "rref":
         return oracle.rref(A, p, want_x=True)["rank"]
+    if op == "trlum":
+        oracle.trlum(A, p)
+        return A.shape[0]
+    if op == "inplace_mm":
+        oracle.inplace_mm(A, A, p)
+        return oracle.cup(A, p)["rank"]
     return oracle.nullspace(A, p)["rank"]
 
 
@@ -406,7 +435,7 @@ def run_ours(args):
               "vs_baseline": None, "dtype": "u32", "data": "synthetic",
               "config": dict({"workload": wname + (" (one persistent launch)" if batched else
                                                    (f", in-place CUP (Algorithm 6), {args.engine} Schur updates" if args.op == "factor" else
-                                                    f", {args.op} through the library (CUP, Algorithms 7-8 or Sec. 5), "
+                                                    f", {args.op} through the library (CUP, Algorithms 5 and 7-9 or Sec. 5), "
                                                     f"{args.engine} Schur updates")),
                               "engine": args.engine, "leading_term_ops": ops,
                               "limbs": cup_limbs(primes[0]) if engine == cup.ENGINE_TENSOR else None,

@@ -278,6 +278,23 @@ cup_status cup_trtri(cup_handle *handle, int flags, uint32_t *T, int64_t ldt, in
  * A <- U L in place. */
 cup_status cup_trulm(cup_handle *handle, uint32_t *A, int64_t lda, int64_t n, uint32_t p, void *stream);
 
+/* TRLUM (Algorithm 5): A = [L\U] n x n with L unit lower triangular stored
+ * strictly below the diagonal and U upper triangular stored on and above it;
+ * A <- L U in place (the product of LU factors, e.g. to rebuild a matrix). */
+cup_status cup_trlum(cup_handle *handle, uint32_t *A, int64_t lda, int64_t n, uint32_t p, void *stream);
+
+/* InPlaceMM (Algorithm 9): B <- A B for A m x m (leading dimension lda >= m) and
+ * B m x n (ldb >= n), row-major device buffers, without an m x n temporary.
+ * A is factored in place by CUP (A = C U P), B is multiplied by P, U and C in
+ * turn (two TRMMs), and A is rebuilt as (C U) P through TRLUM with the unit
+ * diagonal on U; on CUP_OK A holds its original entries again. A may be
+ * singular: the zero blocks of [C\U] storage make the same steps exact.
+ * *rank receives rank(A). Stream-ordered; returns after the work is queued and
+ * the device error word is checked (one synchronisation). A and B must not
+ * overlap. Allocates 2 m int64 words of scratch for the permutation. */
+cup_status cup_inplace_mm(cup_handle *handle, uint32_t *A, int64_t m, int64_t lda, uint32_t *B, int64_t n,
+                          int64_t ldb, uint32_t p, int64_t *rank, void *stream);
+
 /* Allocation-free Schur update: C <- C - A B mod p on the tensor engine,
  * like cup_mm_sub with CUP_ENGINE_TENSOR, for callers that must not allocate
  * device memory (for example code that runs while a stream is being captured

@@ -165,6 +165,35 @@ def mm_sub(Cm, A, B, p: int) -> np.ndarray:
     return Cm
 
 
+def matmul(A, B, p: int) -> np.ndarray:
+    """A B mod p (Algorithm 1 with alpha = 1 on a zero C: the negation of 0 - A B)."""
+    A = _u32arr(A)
+    B = _u32arr(B)
+    neg = mm_sub(np.zeros((A.shape[0], B.shape[1]), dtype=np.uint32), A, B, p).astype(np.uint64)
+    return ((p - neg) % p).astype(np.uint32)
+
+
+def trlum(A, p: int, unit_lower: bool = True) -> np.ndarray:
+    """TRLUM (Algorithm 5) by its definition: A = [L\\U] -> L U.
+
+    unit_lower: L has the implicit unit diagonal and U keeps the stored one
+    (Algorithm 5 as stated); otherwise U is unit and L carries the diagonal,
+    as in the [C\\U] factors of CUP (Algorithm 9)."""
+    A = _u32arr(A)
+    n = A.shape[0]
+    eye = np.eye(n, dtype=np.uint32)
+    if unit_lower:
+        L, U = np.tril(A, -1) + eye, np.triu(A)
+    else:
+        L, U = np.tril(A), np.triu(A, 1) + eye
+    return matmul(L, U, p)
+
+
+def inplace_mm(A, B, p: int) -> np.ndarray:
+    """InPlaceMM (Algorithm 9) by what it computes: A B mod p."""
+    return matmul(A, B, p)
+
+
 def trsm_right_upper_unit(U, B, p: int) -> np.ndarray:
     """TRSM(Right, Upper, Unit): B U^{-1} (Algorithm 2, unit-diagonal variant)."""
     U = _u32arr(U)

@@ -13,7 +13,7 @@ import ctypes
 import os
 
 __all__ = ["load", "Handle", "factor", "rank_profile", "det", "inverse", "rref", "solve",
-           "mm_sub", "trsm_ruu", "laswp_cols", "ENGINE_PLAIN", "ENGINE_TENSOR", "CupError",
+           "ple", "nullspace", "inplace_mm", "mm_sub", "trsm_ruu", "laswp_cols", "ENGINE_PLAIN", "ENGINE_TENSOR", "CupError",
            "LIB_PATH"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -69,6 +69,8 @@ SIGNATURES = {
     "cup_trmm": (_INT, [_P, _INT, _P, _I64, _P, _I64, _I64, _I64, _U32, _P]),
     "cup_trtri": (_INT, [_P, _INT, _P, _I64, _I64, _U32, _P]),
     "cup_trulm": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
+    "cup_trlum": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
+    "cup_inplace_mm": (_INT, [_P, _P, _I64, _I64, _P, _I64, _I64, _U32, _I64P, _P]),
     "cup_mm_sub_noalloc": (_INT, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _P]),
     "cup_factor_batched": (_INT, [_P, _P, _I64, _P, _P, _P]),
 }
@@ -339,6 +341,26 @@ class Handle:
         st = self.lib.cup_trulm(self.h, A.data_ptr(), lda, n, p, _stream_ptr(stream))
         self._check(st, "cup_trulm", self.h)
 
+    def trlum(self, A, p: int, stream=None):
+        """A = [L\\U] (unit lower L, upper U) <- L U in place."""
+        n, n2, lda = _mat(A, "A")
+        if n != n2:
+            raise ValueError("square matrix needed")
+        st = self.lib.cup_trlum(self.h, A.data_ptr(), lda, n, p, _stream_ptr(stream))
+        self._check(st, "cup_trlum", self.h)
+
+    def inplace_mm(self, A, B, p: int, stream=None) -> int:
+        """B <- A B in place (A square, restored on return); returns rank(A)."""
+        m, m2, lda = _mat(A, "A")
+        mb, n, ldb = _mat(B, "B")
+        if m != m2 or mb != m:
+            raise ValueError("A must be m x m and B m x n")
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_inplace_mm(self.h, A.data_ptr(), m, lda, B.data_ptr(), n, ldb, p,
+                                     ctypes.byref(r), _stream_ptr(stream))
+        self._check(st, "cup_inplace_mm", self.h)
+        return int(r.value)
+
     def factor_batched(self, mats, primes, want_det: bool = False, stream=None):
         """Batched in-place CUP: mats is a list of int32 CUDA matrices, primes a list of
         primes. Returns (ranks, profiles, ipivs, dets) as device tensors; profile and
@@ -420,6 +442,10 @@ def ple(A, p, engine=None, stream=None):
 
 def nullspace(A, p, engine=None, stream=None):
     return _handle(engine).nullspace(A, p, stream)
+
+
+def inplace_mm(A, B, p, engine=None, stream=None):
+    return _handle(engine).inplace_mm(A, B, p, stream)
 
 
 def mm_sub(C, A, B, p, engine=ENGINE_TENSOR, stream=None):

@@ -417,6 +417,31 @@ cup_status trulm(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, const ModP 
     return CUP_OK;
 }
 
+// TRLUM (Algorithm 5): A = [L\U] with L lower and U upper triangular; A <- L U.
+// unit_l: L has the implicit unit diagonal (Algorithm 5 as stated); otherwise U
+// has it, as in the [C\U] factors of CUP (Algorithm 9). The halves are done in
+// the order that reads every operand before it is overwritten.
+cup_status trlum(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, int unit_l, const ModP &M, int engine,
+                 cudaStream_t st)
+{
+    if (n <= 0) return CUP_OK;
+    if (n <= 64) {
+        ClassTimer tm(h, st, 4);
+        CU(launch_trlum_leaf(A, lda, (int)n, unit_l, M, st));
+        h->stats.launches += 1;
+        return CUP_OK;
+    }
+    const int64_t k = ((n / 2) + 63) / 64 * 64, n2 = n - k;
+    const int lu = unit_l ? TRI_UNIT : 0, uu = unit_l ? 0 : TRI_UNIT;
+    uint32_t *A11 = A, *A12 = A + k, *A21 = A + k * lda, *A22 = A + k * lda + k;
+    CK(trlum(h, A22, lda, n2, unit_l, M, engine, st));                                  // L3 U3
+    CK(mm_sub(h, A22, lda, A21, lda, A12, lda, n2, n2, k, M, engine, st, 1));           // + L2 U2
+    CK(tri_op(h, TRI_LEFT | lu, A11, lda, A12, lda, k, n2, M, engine, st));             // L1 U2
+    CK(tri_op(h, TRI_UPPER | uu, A11, lda, A21, lda, n2, k, M, engine, st));            // L2 U1
+    CK(trlum(h, A11, lda, k, unit_l, M, engine, st));                                   // L1 U1
+    return CUP_OK;
+}
+
 // Algorithms 7 and 8 on the [C\U] factors of rank r: leaves A as
 // [X1 X2; R2 0] with the rows of C reordered by the profile loop, i.e. the
 // reduced column echelon transform up to that row permutation.
@@ -1189,6 +1214,39 @@ cup_status cup_nullspace(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
     return s;
 }
 
+cup_status cup_inplace_mm(cup_handle *h, uint32_t *A, int64_t m, int64_t lda, uint32_t *B, int64_t n,
+                          int64_t ldb, uint32_t p, int64_t *rank, void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (m > 0 ? m : 1) || ldb < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!A || !B) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t *d_ipiv = nullptr, *d_prof = nullptr;
+    CU(cudaMalloc(&d_ipiv, (size_t)m * sizeof(int64_t)));
+    if (cudaMalloc(&d_prof, (size_t)m * sizeof(int64_t)) != cudaSuccess) {
+        cudaFree(d_ipiv);
+        return CUP_ERR_NOMEM;
+    }
+    int64_t r = 0;
+    const ModP M = make_modp(p);
+    // A = C U P with A <- [C\U]; the zero blocks of that storage make C an m x m
+    // lower and U an m x m unit upper triangle, so A B = C (U (P B)).
+    cup_status s = cup_factor(h, A, m, m, lda, p, d_prof, d_ipiv, &r, stream);
+    if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(B, ldb, n, d_ipiv, r, 0, 0, 0, 0, st));    // B <- P B
+    if (s == CUP_OK) s = tri_op(h, TRI_LEFT | TRI_UPPER | TRI_UNIT, A, lda, B, ldb, m, n, M, h->engine, st);
+    if (s == CUP_OK) s = tri_op(h, TRI_LEFT, A, lda, B, ldb, m, n, M, h->engine, st);          // B <- C B
+    if (s == CUP_OK) s = trlum(h, A, lda, m, 0, M, h->engine, st);                              // A <- C U
+    if (s == CUP_OK) s = cuda_ok(h, launch_col_swaps(A, lda, m, d_ipiv, r, 1, st));             // A <- A P
+    if (s == CUP_OK) s = check_device_error(h, st);
+    if (s == CUP_OK) *rank = r;
+    cudaFree(d_ipiv);
+    cudaFree(d_prof);
+    return s;
+}
+
 cup_status cup_solve(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t *B,
                      int64_t k, int64_t ldb, uint32_t *X, int64_t ldx, uint32_t p, int64_t *rank,
                      void *stream)
@@ -1321,6 +1379,19 @@ cup_status cup_trulm(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, uint32_
     DeviceGuard g(h->device);
     CK(ensure_base(h));
     CK(trulm(h, A, lda, n, make_modp(p), h->engine, (cudaStream_t)stream));
+    CK(check_device_error(h, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+cup_status cup_trlum(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, uint32_t p, void *stream)
+{
+    if (!h || n < 0) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    if (n == 0) return CUP_OK;
+    if (!A || lda < n) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(trlum(h, A, lda, n, 1, make_modp(p), h->engine, (cudaStream_t)stream));
     CK(check_device_error(h, (cudaStream_t)stream));
     return CUP_OK;
 }

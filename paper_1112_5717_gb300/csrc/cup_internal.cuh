@@ -148,6 +148,9 @@ cudaError_t launch_tri_leaf(int flags, const uint32_t *T, int64_t ldt, uint32_t 
 cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st);
 cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int n, ModP M, cudaStream_t st);
 cudaError_t launch_trulm_leaf(uint32_t *A, int64_t lda, int n, ModP M, cudaStream_t st);
+cudaError_t launch_trlum_leaf(uint32_t *A, int64_t lda, int n, int unit_l, ModP M, cudaStream_t st);
+cudaError_t launch_col_swaps(uint32_t *A, int64_t lda, int64_t nrows, const int64_t *list, int64_t count,
+                             int reverse, cudaStream_t st);
 cudaError_t launch_negate(uint32_t *B, int64_t ldb, int64_t m, int64_t n, uint32_t p, cudaStream_t st);
 cudaError_t launch_row_swaps(uint32_t *A, int64_t lda, int64_t ncols, const int64_t *list, int64_t count,
                              int64_t base_a, int64_t base_b, int reverse, int prefix, cudaStream_t st);

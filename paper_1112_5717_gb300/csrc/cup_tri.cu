@@ -724,6 +724,86 @@ cudaError_t launch_trulm_leaf(uint32_t *A, int64_t lda, int n, ModP M, cudaStrea
     return cudaGetLastError();
 }
 
+// TRLUM leaf (Algorithm 5 at its base): A = [L\U], L lower and U upper triangular
+// sharing the block, one of them with an implicit unit diagonal (L if UNIT_L, else U,
+// the [C\U] convention of CUP); A <- L U for an n x n (n <= 64) block.
+template <bool UNIT_L>
+__global__ void __launch_bounds__(256)
+k_trlum_leaf(uint32_t *__restrict__ A, int64_t lda, int n, ModP M)
+{
+    __shared__ uint32_t sA[TRI_MAX][TRI_MAX + 1];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, c = idx - i * n;
+        sA[i][c] = A[i * lda + c];
+    }
+    __syncthreads();
+    uint32_t out[(TRI_MAX * TRI_MAX + 255) / 256];
+    int cnt = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        // (L U)[i][j] = sum_{k <= min(i, j)} L[i][k] U[k][j]; the k = min(i, j) term
+        // carries the unit diagonal of one factor.
+        Acc acc = {0ull, 0u};
+        const int kd = i < j ? i : j;
+        for (int k = 0; k < kd; ++k) acc_add(acc, (uint64_t)sA[i][k] * sA[k][j]);
+        const bool plain = UNIT_L ? (i <= j) : (i >= j);     // the unit factor meets the term
+        acc_add(acc, plain ? (uint64_t)sA[i][j] : (uint64_t)sA[i][j] * sA[kd][kd]);
+        out[cnt++] = acc_red(acc, M);
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        A[i * lda + j] = out[cnt++];
+    }
+}
+
+cudaError_t launch_trlum_leaf(uint32_t *A, int64_t lda, int n, int unit_l, ModP M, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n > TRI_MAX) return cudaErrorInvalidValue;
+    if (unit_l) k_trlum_leaf<true><<<1, 256, 0, st>>>(A, lda, n, M);
+    else k_trlum_leaf<false><<<1, 256, 0, st>>>(A, lda, n, M);
+    return cudaGetLastError();
+}
+
+// Column transpositions (t, list[t]) for t in [0, count) applied to rows
+// 0..nrows-1, in order or (reverse) in reverse order; one thread per row, the
+// list staged through shared memory a chunk at a time.
+__global__ void __launch_bounds__(256)
+k_col_swaps(uint32_t *__restrict__ A, int64_t lda, int64_t nrows, const int64_t *__restrict__ list,
+            int64_t count, int reverse)
+{
+    __shared__ int64_t sl[256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t *row = A + i * lda;
+    for (int64_t b = 0; b < count; b += 256) {
+        const int64_t e = (count - b) < 256 ? (count - b) : 256;
+        __syncthreads();
+        if (threadIdx.x < e) {
+            const int64_t s = b + threadIdx.x;
+            sl[threadIdx.x] = list[reverse ? count - 1 - s : s];
+        }
+        __syncthreads();
+        if (i < nrows)
+            for (int64_t k = 0; k < e; ++k) {
+                const int64_t t = reverse ? count - 1 - (b + k) : b + k, c = sl[k];
+                if (c == t) continue;
+                const uint32_t x = row[t];
+                row[t] = row[c];
+                row[c] = x;
+            }
+    }
+}
+
+cudaError_t launch_col_swaps(uint32_t *A, int64_t lda, int64_t nrows, const int64_t *list, int64_t count,
+                             int reverse, cudaStream_t st)
+{
+    if (nrows <= 0 || count <= 0) return cudaSuccess;
+    k_col_swaps<<<(unsigned)((nrows + 255) / 256), 256, 0, st>>>(A, lda, nrows, list, count, reverse);
+    return cudaGetLastError();
+}
+
 // Zero the strict upper triangle of an n x n block.
 __global__ void k_zero_upper(uint32_t *__restrict__ B, int64_t ldb, int64_t n)
 {

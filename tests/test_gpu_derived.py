@@ -214,3 +214,34 @@ def test_ple(handle, m, n, r, p):
     assert np.array_equal(prof.cpu().numpy(), want["profile"])
     assert np.array_equal(ipiv.cpu().numpy(), want["ipiv"])
     assert np.array_equal(_host(dA), want["packed"].astype(np.int64))
+
+
+@pytest.mark.parametrize("n,p", [(1, 7), (40, 65521), (64, 3), (97, 8388593), (260, 2147483647)])
+def test_trlum(handle, n, p):
+    """Algorithm 5: [L\\U] <- L U, checked against the product of the split factors."""
+    rng = np.random.default_rng(n + 7)
+    A = rng.integers(0, p, size=(n, n))
+    want = oracle.trlum(A, p, unit_lower=True)
+    dA = _dev(A)
+    handle.trlum(dA, p)
+    assert np.array_equal(_host(dA), want)
+
+
+@pytest.mark.parametrize("m,n,p,rank", [(1, 1, 7, 1), (40, 13, 65521, 40), (64, 64, 3, 64),
+                                        (97, 150, 8388593, 97), (130, 70, 2147483647, 130),
+                                        (200, 33, 65521, 117), (129, 65, 2, 50), (70, 20, 251, 0)])
+def test_inplace_mm(handle, m, n, p, rank):
+    """Algorithm 9: B <- A B through CUP, two TRMMs and TRLUM; A comes back unchanged."""
+    rng = np.random.default_rng(m * 31 + n + rank)
+    if rank == m:
+        A = rng.integers(0, p, size=(m, m))
+    else:
+        A = exact_matmul_mod(rng.integers(0, p, size=(m, rank)), rng.integers(0, p, size=(rank, m)), p)
+    B = rng.integers(0, p, size=(m, n))
+    want = oracle.inplace_mm(A, B, p)
+    dA = _dev(A)
+    dB = _dev(B)
+    r = handle.inplace_mm(dA, dB, p)
+    assert np.array_equal(_host(dB), want)
+    assert np.array_equal(_host(dA), A % p)
+    assert r == oracle.cup(A % p, p)["rank"]

@@ -443,3 +443,52 @@ def test_oracle_ple_reconstructs_and_reveals_the_column_profile(m, n, r, p):
     assert all(a < b for a, b in zip(lead, lead[1:]))
     if p ** min(m, n) <= 4096:
         assert lead == span_profile(np.asarray(A).T, p)
+
+
+@pytest.mark.parametrize("n,p", [(1, 7), (5, 13), (16, 65521), (23, 2147483647)])
+def test_oracle_trlum_is_the_triangle_product(n, p):
+    """TRLUM (Algorithm 5) against Python-integer products of the two triangles,
+    taken entry by entry from the sum over k <= min(i, j)."""
+    rng = np.random.default_rng(n + p % 97)
+    A = rng.integers(0, p, size=(n, n))
+    for unit_lower in (True, False):
+        got = oracle.trlum(A, p, unit_lower)
+        for i in range(n):
+            for j in range(n):
+                acc = 0
+                for k in range(min(i, j) + 1):
+                    lik = (1 if k == i else int(A[i, k])) if unit_lower else int(A[i, k])
+                    ukj = int(A[k, j]) if unit_lower else (1 if k == j else int(A[k, j]))
+                    acc += lik * ukj
+                assert int(got[i, j]) == acc % p
+
+
+@pytest.mark.parametrize("m,n,r,p", [(6, 6, 6, 7), (12, 12, 7, 65521), (9, 9, 0, 5), (10, 10, 10, 2)])
+def test_oracle_trlum_rebuilds_cup(m, n, r, p):
+    """The unit-U TRLUM of CUP's packed [C\\U] is A P^T (Proposition 1), also
+    when A is singular (the zero blocks of the storage), and U = I, C = A
+    reduces it to the identity map on a lower-triangular A."""
+    rng = np.random.default_rng(m * 13 + r)
+    A = low_rank(rng, m, n, r, p)
+    d = oracle.cup_packed(A, p)
+    Pt = perm_matrix_from_ipiv(d["ipiv"], n)
+    assert np.array_equal(oracle.trlum(d["packed"], p, unit_lower=False).astype(np.int64),
+                          exact_matmul_mod(A, Pt, p))
+    Lw = np.tril(rng.integers(0, p, size=(m, m)))
+    assert np.array_equal(oracle.trlum(Lw, p, unit_lower=False), Lw)
+    Uw = np.triu(rng.integers(0, p, size=(m, m)))
+    assert np.array_equal(oracle.trlum(Uw, p, unit_lower=True), Uw)
+
+
+@pytest.mark.parametrize("m,n,p", [(1, 3, 7), (8, 5, 65521), (13, 13, 2147483647)])
+def test_oracle_inplace_mm_is_the_product(m, n, p):
+    """InPlaceMM (Algorithm 9) computes A B: exact integer product, identity and
+    associativity (A (B v) = (A B) v)."""
+    rng = np.random.default_rng(m + n)
+    A = rng.integers(0, p, size=(m, m))
+    B = rng.integers(0, p, size=(m, n))
+    got = oracle.inplace_mm(A, B, p).astype(np.int64)
+    assert np.array_equal(got, exact_matmul_mod(A, B, p))
+    assert np.array_equal(oracle.inplace_mm(np.eye(m, dtype=np.int64), B, p).astype(np.int64), B)
+    v = rng.integers(0, p, size=(n, 1))
+    assert np.array_equal(exact_matmul_mod(got, v, p), exact_matmul_mod(A, exact_matmul_mod(B, v, p), p))
