@@ -233,6 +233,55 @@ typedef struct {
 cup_status cup_factor_batched(cup_handle *handle, const cup_batch_item *d_items, int64_t count,
                               int64_t *d_rank, uint32_t *d_det, void *stream);
 
+/* ---- Integer matrices by multi-modular reduction (Sec. 1: computations over
+ * Z reduce to linear algebra over prime fields by homomorphic imaging) ----
+ * The integer matrix is reduced modulo several primes on the device, each
+ * image is factored by CUP (Algorithm 6; the batched launch for images with
+ * min(m, n) <= 512, one full-device factorisation per prime otherwise), and
+ * the residues are combined on the host by the Chinese remainder theorem.
+ * A is a DEVICE int64 matrix, row-major with leading dimension lda >= n;
+ * `primes` is a HOST array of K distinct primes below 2^31, or NULL to let
+ * the library take the largest primes below 2^31, as many as the bound
+ * requires. Integer results are returned as a sign (-1, 0, 1) and the
+ * magnitude in little-endian 32-bit words. All calls synchronise the stream. */
+
+/* log2 of the product of the Euclidean norms of the nonzero rows of A (m x n):
+ * bounds |det A| (Hadamard's inequality) and every minor of A. */
+cup_status cup_int_bound(cup_handle *handle, const int64_t *A, int64_t m, int64_t n, int64_t lda,
+                         double *log2_bound, void *stream);
+
+/* det A for square integer A (n x n). *sign and words[0 .. *nwords) receive
+ * the integer congruent to det A modulo the product M of the primes used, in
+ * (-M/2, M/2]; *certified is 1 when M > 2 * (Hadamard bound), so that this is
+ * det A exactly. *rank receives the largest rank over the primes (a lower
+ * bound on the rank over Q, exact when certified) and *nprimes (if not NULL)
+ * the number of primes used. Returns CUP_ERR_TOO_LARGE, with *nwords set, when
+ * cap words are too few (size cap from cup_int_bound: ceil((bound + 1) / 32) + 1
+ * always suffices for a certified result). */
+cup_status cup_int_det(cup_handle *handle, const int64_t *A, int64_t n, int64_t lda, const uint32_t *primes,
+                       int64_t K, uint32_t *words, int64_t cap, int64_t *nwords, int *sign, int64_t *rank,
+                       int *certified, int64_t *nprimes, void *stream);
+
+/* rank over Q of the integer matrix A (m x n): the largest rank of its images.
+ * *certified is 1 when the product of the primes exceeds the minor bound of
+ * cup_int_bound: then no nonzero maximal minor vanishes modulo all of them,
+ * so the rank is exact. */
+cup_status cup_int_rank(cup_handle *handle, const int64_t *A, int64_t m, int64_t n, int64_t lda,
+                        const uint32_t *primes, int64_t K, int64_t *rank, int *certified, int64_t *nprimes,
+                        void *stream);
+
+/* Host only. The integer x with x = residues[i] (mod primes[i]) for all i < K,
+ * in the symmetric range (-M/2, M/2] of M = product of the primes (mixed-radix
+ * Chinese remaindering). Primes must be distinct primes below 2^31
+ * (CUP_ERR_PRIME / CUP_ERR_ARG otherwise); CUP_ERR_TOO_LARGE with *nwords set
+ * when cap words are too few. */
+cup_status cup_crt(const uint32_t *residues, const uint32_t *primes, int64_t K, uint32_t *words, int64_t cap,
+                   int64_t *nwords, int *sign);
+
+/* Host only. The `count` largest primes below `bound`, descending, into out;
+ * *found receives how many exist (fewer when bound is small). */
+cup_status cup_primes_below(uint32_t bound, int64_t count, uint32_t *out, int64_t *found);
+
 /* ---- Building blocks of the hot path (exposed for testing and reuse) ---- */
 
 /* Schur update (Algorithm 1, alpha = -1, beta = 1): C <- C - A B mod p.

@@ -290,6 +290,53 @@ def solve(A, B, p: int):
     return int(s), X, d["rank"]
 
 
+def int_det(A) -> int:
+    """det of an integer matrix over Z by fraction-free (Bareiss) elimination on
+    Python integers: exact, for the small sizes the tests use. It is the value
+    the multi-modular path must reconstruct (Sec. 1: integer problems reduced to
+    prime fields)."""
+    M = [[int(x) for x in row] for row in np.asarray(A)]
+    n = len(M)
+    if n == 0:
+        return 1
+    sign, prev = 1, 1
+    for k in range(n - 1):
+        if M[k][k] == 0:
+            sw = next((i for i in range(k + 1, n) if M[i][k] != 0), None)
+            if sw is None:
+                return 0
+            M[k], M[sw] = M[sw], M[k]
+            sign = -sign
+        for i in range(k + 1, n):
+            for j in range(k + 1, n):
+                M[i][j] = (M[i][j] * M[k][k] - M[i][k] * M[k][j]) // prev
+        prev = M[k][k]
+    return sign * M[n - 1][n - 1]
+
+
+def int_rank(A) -> int:
+    """rank over Q of an integer matrix: Gaussian elimination on exact rationals
+    (Python fractions), for the small sizes the tests use."""
+    from fractions import Fraction
+    M = [[Fraction(int(x)) for x in row] for row in np.asarray(A)]
+    m = len(M)
+    n = len(M[0]) if m else 0
+    r = 0
+    for c in range(n):
+        piv = next((i for i in range(r, m) if M[i][c] != 0), None)
+        if piv is None:
+            continue
+        M[r], M[piv] = M[piv], M[r]
+        for i in range(r + 1, m):
+            if M[i][c]:
+                f = M[i][c] / M[r][c]
+                M[i] = [x - f * y for x, y in zip(M[i], M[r])]
+        r += 1
+        if r == m:
+            break
+    return r
+
+
 def opcount(m: int, n: int, profile) -> float:
     prof = np.ascontiguousarray(profile, dtype=np.int64)
     if prof.size == 0:

@@ -13,7 +13,7 @@ import ctypes
 import os
 
 __all__ = ["load", "Handle", "factor", "rank_profile", "det", "inverse", "rref", "solve",
-           "ple", "nullspace", "inplace_mm", "mm_sub", "trsm_ruu", "laswp_cols", "ENGINE_PLAIN", "ENGINE_TENSOR", "CupError",
+           "ple", "nullspace", "inplace_mm", "int_det", "int_rank", "crt", "primes_below", "mm_sub", "trsm_ruu", "laswp_cols", "ENGINE_PLAIN", "ENGINE_TENSOR", "CupError",
            "LIB_PATH"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -46,6 +46,8 @@ _U32 = ctypes.c_uint32
 _INT = ctypes.c_int
 _I64P = ctypes.POINTER(ctypes.c_int64)
 _U32P = ctypes.POINTER(ctypes.c_uint32)
+_INTP = ctypes.POINTER(ctypes.c_int)
+_DBLP = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "cup_create": (_INT, [ctypes.POINTER(_P), _INT]),
     "cup_destroy": (_INT, [_P]),
@@ -71,6 +73,11 @@ SIGNATURES = {
     "cup_trulm": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
     "cup_trlum": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
     "cup_inplace_mm": (_INT, [_P, _P, _I64, _I64, _P, _I64, _I64, _U32, _I64P, _P]),
+    "cup_int_bound": (_INT, [_P, _P, _I64, _I64, _I64, _DBLP, _P]),
+    "cup_int_det": (_INT, [_P, _P, _I64, _I64, _U32P, _I64, _U32P, _I64, _I64P, _INTP, _I64P, _INTP, _I64P, _P]),
+    "cup_int_rank": (_INT, [_P, _P, _I64, _I64, _I64, _U32P, _I64, _I64P, _INTP, _I64P, _P]),
+    "cup_crt": (_INT, [_U32P, _U32P, _I64, _U32P, _I64, _I64P, _INTP]),
+    "cup_primes_below": (_INT, [_U32, _I64, _U32P, _I64P]),
     "cup_mm_sub_noalloc": (_INT, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _P]),
     "cup_factor_batched": (_INT, [_P, _P, _I64, _P, _P, _P]),
 }
@@ -131,6 +138,29 @@ def _mat(t, what):
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError(f"{what} must be a row-major 2-D tensor (unit column stride)")
     return t.shape[0], t.shape[1], max(t.stride(0), 1)
+
+
+def _imat(t, what):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int64:
+        raise TypeError(f"{what} must be a CUDA torch.int64 tensor of integers")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{what} must be a row-major 2-D tensor (unit column stride)")
+    return t.shape[0], t.shape[1], max(t.stride(0), 1)
+
+
+def _prime_array(primes):
+    if primes is None:
+        return None, 0
+    arr = (ctypes.c_uint32 * len(primes))(*[int(q) for q in primes])
+    return arr, len(primes)
+
+
+def _from_words(words, nwords: int, sign: int) -> int:
+    mag = 0
+    for i in range(nwords - 1, -1, -1):
+        mag = (mag << 32) | int(words[i])
+    return -mag if sign < 0 else mag
 
 
 class Handle:
@@ -361,6 +391,47 @@ class Handle:
         self._check(st, "cup_inplace_mm", self.h)
         return int(r.value)
 
+    def int_bound(self, A, stream=None) -> float:
+        """log2 of the product of the nonzero rows' Euclidean norms of an int64 matrix."""
+        m, n, lda = _imat(A, "A")
+        b = ctypes.c_double(0.0)
+        st = self.lib.cup_int_bound(self.h, A.data_ptr(), m, n, lda, ctypes.byref(b), _stream_ptr(stream))
+        self._check(st, "cup_int_bound", self.h)
+        return float(b.value)
+
+    def int_det(self, A, primes=None, stream=None):
+        """det of a square int64 matrix by CUP modulo primes and CRT.
+        Returns (det, rank, certified, number of primes used)."""
+        n, n2, lda = _imat(A, "A")
+        if n != n2:
+            raise ValueError("int_det needs a square matrix")
+        cap = int(self.int_bound(A, stream) + 33.0) // 32 + 2 if primes is None else len(primes) + 2
+        parr, K = _prime_array(primes)
+        nw, sg, rk, cert, npr = (ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int(0),
+                                 ctypes.c_int64(0))
+        for _ in range(2):
+            words = (ctypes.c_uint32 * max(cap, 1))()
+            st = self.lib.cup_int_det(self.h, A.data_ptr(), n, lda, parr, K, words, cap, ctypes.byref(nw),
+                                      ctypes.byref(sg), ctypes.byref(rk), ctypes.byref(cert), ctypes.byref(npr),
+                                      _stream_ptr(stream))
+            if st == -8 and nw.value > cap:
+                cap = nw.value
+                continue
+            break
+        self._check(st, "cup_int_det", self.h)
+        return _from_words(words, nw.value, sg.value), int(rk.value), bool(cert.value), int(npr.value)
+
+    def int_rank(self, A, primes=None, stream=None):
+        """rank over Q of an int64 matrix by CUP modulo primes.
+        Returns (rank, certified, number of primes used)."""
+        m, n, lda = _imat(A, "A")
+        parr, K = _prime_array(primes)
+        rk, cert, npr = ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_int64(0)
+        st = self.lib.cup_int_rank(self.h, A.data_ptr(), m, n, lda, parr, K, ctypes.byref(rk), ctypes.byref(cert),
+                                   ctypes.byref(npr), _stream_ptr(stream))
+        self._check(st, "cup_int_rank", self.h)
+        return int(rk.value), bool(cert.value), int(npr.value)
+
     def factor_batched(self, mats, primes, want_det: bool = False, stream=None):
         """Batched in-place CUP: mats is a list of int32 CUDA matrices, primes a list of
         primes. Returns (ranks, profiles, ipivs, dets) as device tensors; profile and
@@ -446,6 +517,42 @@ def nullspace(A, p, engine=None, stream=None):
 
 def inplace_mm(A, B, p, engine=None, stream=None):
     return _handle(engine).inplace_mm(A, B, p, stream)
+
+
+def int_det(A, primes=None, engine=None, stream=None):
+    return _handle(engine).int_det(A, primes, stream)
+
+
+def int_rank(A, primes=None, engine=None, stream=None):
+    return _handle(engine).int_rank(A, primes, stream)
+
+
+def crt(residues, primes) -> int:
+    """The integer in (-M/2, M/2] congruent to residues[i] mod primes[i] (host, no GPU)."""
+    lib = load()
+    K = len(primes)
+    if K != len(residues):
+        raise ValueError("one residue per prime")
+    r = (ctypes.c_uint32 * K)(*[int(x) for x in residues])
+    q = (ctypes.c_uint32 * K)(*[int(x) for x in primes])
+    cap = K + 2
+    words = (ctypes.c_uint32 * cap)()
+    nw, sg = ctypes.c_int64(0), ctypes.c_int(0)
+    st = lib.cup_crt(r, q, K, words, cap, ctypes.byref(nw), ctypes.byref(sg))
+    if st != 0:
+        raise CupError(st, "cup_crt", "")
+    return _from_words(words, nw.value, sg.value)
+
+
+def primes_below(bound: int, count: int) -> list:
+    """The `count` largest primes below `bound`, descending (host, no GPU)."""
+    lib = load()
+    out = (ctypes.c_uint32 * max(count, 1))()
+    found = ctypes.c_int64(0)
+    st = lib.cup_primes_below(int(bound), int(count), out, ctypes.byref(found))
+    if st != 0:
+        raise CupError(st, "cup_primes_below", "")
+    return [int(out[i]) for i in range(found.value)]
 
 
 def mm_sub(C, A, B, p, engine=ENGINE_TENSOR, stream=None):

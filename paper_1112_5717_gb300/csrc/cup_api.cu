@@ -17,6 +17,8 @@
 //     found, so P <- Diag(I_r1, P2) P1 and the profile offsets need no work.
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <new>
 #include <vector>
@@ -1409,6 +1411,268 @@ cup_status cup_factor_batched(cup_handle *h, const cup_batch_item *d_items, int6
     const int64_t grid = count < (int64_t)nsm * 2 ? count : (int64_t)nsm * 2;
     CU(launch_cup_batched(d_items, count, d_rank, d_det, h->d_next, (int)grid, (cudaStream_t)stream));
     h->stats.launches += 1;
+    return CUP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Multi-modular integer determinant and rank (Sec. 1: reduction to prime fields)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+const int64_t INT_BATCH_MAX = 512;   // images of this size or less are factored together in one launch
+
+// log2 of the product of the Euclidean norms of the nonzero rows of A: a bound
+// on |det A| (Hadamard) and on every minor of A.
+cup_status int_bound(cup_handle *h, const int64_t *A, int64_t m, int64_t n, int64_t lda, double *out, cudaStream_t st)
+{
+    *out = 0.0;
+    if (m == 0 || n == 0) return CUP_OK;
+    double *d = nullptr;
+    CU(cudaMalloc(&d, (size_t)m * sizeof(double)));
+    std::vector<double> v((size_t)m);
+    cup_status s = cuda_ok(h, launch_row_log2norm(A, lda, m, n, d, st));
+    if (s == CUP_OK)
+        s = cuda_ok(h, cudaMemcpyAsync(v.data(), d, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (s == CUP_OK) s = sync_stream(h, st);
+    cudaFree(d);
+    CK(s);
+    double sum = 0.0;
+    for (double x : v)
+        if (x > 0.0) sum += x;            // zero rows (-1e300) and unit rows add nothing
+    *out = sum * (1.0 + 1e-12) + 1e-9;    // the host sum's rounding, upward
+    return CUP_OK;
+}
+
+// The primes to use: the caller's (checked: prime, below 2^31, pairwise distinct),
+// or, if none are given, the largest primes below 2^31 until their product exceeds
+// 2^need.
+cup_status int_primes(const uint32_t *given, int64_t K, double need, std::vector<uint32_t> &out)
+{
+    out.clear();
+    if (given) {
+        if (K <= 0) return CUP_ERR_ARG;
+        out.assign(given, given + K);
+        for (uint32_t q : out) CK(check_prime(q));
+        std::vector<uint32_t> srt = out;
+        std::sort(srt.begin(), srt.end());
+        for (size_t i = 1; i < srt.size(); ++i)
+            if (srt[i] == srt[i - 1]) return CUP_ERR_ARG;
+        return CUP_OK;
+    }
+    double have = 0.0;
+    uint32_t q = 1u << 31;
+    while (out.empty() || have <= need) {
+        uint32_t nx = 0;
+        if (cup_internal_primes_below(q, 1, &nx) != 1) return CUP_ERR_UNSUPPORTED;
+        out.push_back(nx);
+        have += std::log2((double)nx);
+        q = nx;
+    }
+    return CUP_OK;
+}
+
+double log2_product(const std::vector<uint32_t> &pr)
+{
+    double s = 0.0;
+    for (uint32_t q : pr) s += std::log2((double)q);
+    return s * (1.0 - 1e-12);             // downward
+}
+
+// rank (and det, square A) of A mod each prime: batched CUP for small images,
+// one full-device CUP per prime otherwise.
+cup_status int_residues(cup_handle *h, const int64_t *A, int64_t m, int64_t n, int64_t lda,
+                        const std::vector<uint32_t> &pr, int64_t *ranks, uint32_t *dets, cudaStream_t st)
+{
+    const int64_t K = (int64_t)pr.size();
+    const int64_t kmn = m < n ? m : n;
+    const int64_t mx = m > n ? m : n;
+    const size_t plane = (size_t)m * (size_t)n;
+    uint32_t *d_pr = nullptr;
+    CU(cudaMalloc(&d_pr, (size_t)K * sizeof(uint32_t)));
+    cup_status s = cuda_ok(h, cudaMemcpyAsync(d_pr, pr.data(), (size_t)K * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    const bool batched = kmn <= INT_BATCH_MAX && mx <= 2048 && (double)K * (double)plane * 4.0 <= 4.0 * (1ull << 30);
+    if (s == CUP_OK && batched) {
+        // one allocation: residue planes | profile+ipiv per image | items | ranks | dets
+        const size_t b_res = (size_t)K * plane * 4, b_idx = (size_t)K * 2 * (size_t)kmn * 8,
+                     b_items = (size_t)K * sizeof(cup_batch_item), b_rank = (size_t)K * 8, b_det = (size_t)K * 4;
+        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        char *base = nullptr;
+        s = cuda_ok(h, cudaMalloc(&base, up(b_res) + up(b_idx) + up(b_items) + up(b_rank) + up(b_det)));
+        if (s == CUP_OK) {
+            uint32_t *R = (uint32_t *)base;
+            int64_t *d_idx = (int64_t *)(base + up(b_res));
+            cup_batch_item *d_items = (cup_batch_item *)(base + up(b_res) + up(b_idx));
+            int64_t *d_rank = (int64_t *)((char *)d_items + up(b_items));
+            uint32_t *d_det = (uint32_t *)((char *)d_rank + up(b_rank));
+            std::vector<cup_batch_item> items((size_t)K);
+            for (int64_t k = 0; k < K; ++k) {
+                cup_batch_item &it = items[(size_t)k];
+                memset(&it, 0, sizeof(it));
+                it.A = R + (size_t)k * plane;
+                it.m = m;
+                it.n = n;
+                it.lda = n;
+                it.p = pr[(size_t)k];
+                it.profile = d_idx + (size_t)k * 2 * (size_t)kmn;
+                it.ipiv = it.profile + kmn;
+            }
+            std::vector<int64_t> hr((size_t)K);
+            std::vector<uint32_t> hd((size_t)K);
+            s = cuda_ok(h, launch_reduce_multi(A, lda, m, n, d_pr, (int)K, R, n, (int64_t)plane, st));
+            if (s == CUP_OK)
+                s = cuda_ok(h, cudaMemcpyAsync(d_items, items.data(), b_items, cudaMemcpyHostToDevice, st));
+            if (s == CUP_OK) s = cup_factor_batched(h, d_items, K, d_rank, dets ? d_det : nullptr, st);
+            if (s == CUP_OK) s = cuda_ok(h, cudaMemcpyAsync(hr.data(), d_rank, b_rank, cudaMemcpyDeviceToHost, st));
+            if (s == CUP_OK && dets)
+                s = cuda_ok(h, cudaMemcpyAsync(hd.data(), d_det, b_det, cudaMemcpyDeviceToHost, st));
+            if (s == CUP_OK) s = sync_stream(h, st);
+            h->stats.launches += 1;
+            for (int64_t k = 0; s == CUP_OK && k < K; ++k) {
+                if (hr[(size_t)k] < 0) s = CUP_ERR_CUDA;
+                ranks[k] = hr[(size_t)k];
+                if (dets) dets[k] = hd[(size_t)k];
+            }
+            cudaFree(base);
+        }
+    } else if (s == CUP_OK) {
+        uint32_t *buf = nullptr, *d_out = nullptr;
+        int64_t *d_idx = nullptr;
+        s = cuda_ok(h, cudaMalloc(&buf, plane * 4));
+        if (s == CUP_OK) s = cuda_ok(h, cudaMalloc(&d_idx, 2 * (size_t)kmn * sizeof(int64_t)));
+        if (s == CUP_OK) s = cuda_ok(h, cudaMalloc(&d_out, sizeof(uint32_t)));
+        for (int64_t k = 0; s == CUP_OK && k < K; ++k) {
+            const uint32_t q = pr[(size_t)k];
+            int64_t r = 0;
+            s = cuda_ok(h, launch_reduce_multi(A, lda, m, n, d_pr + k, 1, buf, n, (int64_t)plane, st));
+            h->stats.launches += 1;
+            if (s == CUP_OK) s = cup_factor(h, buf, m, n, n, q, d_idx, d_idx + kmn, &r, st);
+            if (s != CUP_OK) break;
+            ranks[k] = r;
+            if (!dets) continue;
+            if (m != n || r < n) {
+                dets[k] = 0;
+                continue;
+            }
+            s = cuda_ok(h, launch_det_reduce(buf, n, n, d_idx + kmn, make_modp(q), d_out, st));
+            h->stats.launches += 1;
+            if (s == CUP_OK)
+                s = cuda_ok(h, cudaMemcpyAsync(h->h_pinned, d_out, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            if (s == CUP_OK) s = sync_stream(h, st);
+            if (s == CUP_OK) dets[k] = (uint32_t)h->h_pinned[0];
+        }
+        if (buf) cudaFree(buf);
+        if (d_idx) cudaFree(d_idx);
+        if (d_out) cudaFree(d_out);
+    }
+    cudaFree(d_pr);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+cup_status cup_primes_below(uint32_t bound, int64_t count, uint32_t *out, int64_t *found)
+{
+    if (!found || count < 0 || (count > 0 && !out)) return CUP_ERR_ARG;
+    *found = cup_internal_primes_below(bound, count, out);
+    return CUP_OK;
+}
+
+cup_status cup_crt(const uint32_t *residues, const uint32_t *primes, int64_t K, uint32_t *words, int64_t cap,
+                   int64_t *nwords, int *sign)
+{
+    if (!residues || !primes || !nwords || !sign || K <= 0 || cap < 0 || (cap > 0 && !words)) return CUP_ERR_ARG;
+    for (int64_t i = 0; i < K; ++i) CK(check_prime(primes[i]));
+    std::vector<uint32_t> mag;
+    int sg = 0;
+    if (!cup_internal_crt(residues, primes, K, mag, sg)) return CUP_ERR_ARG;
+    *nwords = (int64_t)mag.size();
+    *sign = sg;
+    if ((int64_t)mag.size() > cap) return CUP_ERR_TOO_LARGE;
+    if (!mag.empty()) memcpy(words, mag.data(), mag.size() * sizeof(uint32_t));
+    return CUP_OK;
+}
+
+cup_status cup_int_bound(cup_handle *h, const int64_t *A, int64_t m, int64_t n, int64_t lda, double *log2_bound,
+                         void *stream)
+{
+    if (!h || !log2_bound || m < 0 || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    if (m > 0 && n > 0 && !A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    return int_bound(h, A, m, n, lda, log2_bound, (cudaStream_t)stream);
+}
+
+cup_status cup_int_det(cup_handle *h, const int64_t *A, int64_t n, int64_t lda, const uint32_t *primes, int64_t K,
+                       uint32_t *words, int64_t cap, int64_t *nwords, int *sign, int64_t *rank, int *certified,
+                       int64_t *nprimes, void *stream)
+{
+    if (!h || !nwords || !sign || !rank || !certified || n < 0 || lda < (n > 0 ? n : 1) || cap < 0 ||
+        (cap > 0 && !words))
+        return CUP_ERR_ARG;
+    *rank = 0;
+    *certified = 0;
+    if (nprimes) *nprimes = 0;
+    if (n == 0) {
+        *nwords = 1;
+        *sign = 1;
+        *certified = 1;
+        if (cap < 1) return CUP_ERR_TOO_LARGE;
+        words[0] = 1;
+        return CUP_OK;
+    }
+    if (!A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    double bound = 0.0;
+    CK(int_bound(h, A, n, n, lda, &bound, st));
+    std::vector<uint32_t> pr;
+    CK(int_primes(primes, K, bound + 1.0, pr));     // the symmetric range needs M > 2 |det|
+    const int64_t Kp = (int64_t)pr.size();
+    std::vector<int64_t> ranks((size_t)Kp);
+    std::vector<uint32_t> dets((size_t)Kp);
+    CK(ensure_base(h));
+    CK(int_residues(h, A, n, n, lda, pr, ranks.data(), dets.data(), st));
+    int64_t r = 0;
+    for (int64_t x : ranks) r = x > r ? x : r;
+    std::vector<uint32_t> mag;
+    int sg = 0;
+    if (!cup_internal_crt(dets.data(), pr.data(), Kp, mag, sg)) return CUP_ERR_ARG;
+    *rank = r;
+    *certified = log2_product(pr) > bound + 1.0;
+    if (nprimes) *nprimes = Kp;
+    *nwords = (int64_t)mag.size();
+    *sign = sg;
+    if ((int64_t)mag.size() > cap) return CUP_ERR_TOO_LARGE;
+    if (!mag.empty()) memcpy(words, mag.data(), mag.size() * sizeof(uint32_t));
+    return CUP_OK;
+}
+
+cup_status cup_int_rank(cup_handle *h, const int64_t *A, int64_t m, int64_t n, int64_t lda, const uint32_t *primes,
+                        int64_t K, int64_t *rank, int *certified, int64_t *nprimes, void *stream)
+{
+    if (!h || !rank || !certified || m < 0 || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    *rank = 0;
+    *certified = 1;
+    if (nprimes) *nprimes = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    double bound = 0.0;
+    CK(int_bound(h, A, m, n, lda, &bound, st));
+    std::vector<uint32_t> pr;
+    CK(int_primes(primes, K, bound, pr));           // not every prime can divide a nonzero minor
+    std::vector<int64_t> ranks(pr.size());
+    CK(ensure_base(h));
+    CK(int_residues(h, A, m, n, lda, pr, ranks.data(), nullptr, st));
+    int64_t r = 0;
+    for (int64_t x : ranks) r = x > r ? x : r;
+    *rank = r;
+    *certified = log2_product(pr) > bound;
+    if (nprimes) *nprimes = (int64_t)pr.size();
     return CUP_OK;
 }
 

@@ -168,3 +168,14 @@ cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t 
 bool cup_internal_prime_ok(uint32_t p);
 
 // Batched CUP (cup_batched.cu).
+
+// Multi-modular integer path (cup_int.cu).
+#include <vector>
+cudaError_t launch_reduce_multi(const int64_t *A, int64_t lda, int64_t m, int64_t n, const uint32_t *d_primes,
+                                int K, uint32_t *R, int64_t ldr, int64_t plane, cudaStream_t st);
+cudaError_t launch_row_log2norm(const int64_t *A, int64_t lda, int64_t m, int64_t n, double *out, cudaStream_t st);
+// x = CRT(res mod pr) in the symmetric range, as sign and little-endian 32-bit magnitude
+// words; false if two primes coincide.
+bool cup_internal_crt(const uint32_t *res, const uint32_t *pr, int64_t K, std::vector<uint32_t> &mag, int &sign);
+bool cup_internal_is_prime(uint32_t n);
+int64_t cup_internal_primes_below(uint32_t bound, int64_t count, uint32_t *out);

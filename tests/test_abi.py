@@ -61,3 +61,65 @@ def test_null_handle_is_rejected(lib_path):
     assert lib.cup_factor(None, None, 0, 0, 1, 7, None, None, ctypes.byref(r), None) == -1
     assert lib.cup_set_option(None, 0, 0) == -1
     assert lib.cup_destroy(None) == -1
+
+
+def _trial_prime(q: int) -> bool:
+    if q < 2:
+        return False
+    d = 2
+    while d * d <= q:
+        if q % d == 0:
+            return False
+        d += 1
+    return True
+
+
+def test_primes_below_against_trial_division(lib_path):
+    """Host prime generator of the multi-modular path: the largest primes below a bound."""
+    import paper_1112_5717_gb300 as cup
+    got = cup.primes_below(1 << 31, 12)
+    want, q = [], (1 << 31) - 1
+    while len(want) < 12:
+        if _trial_prime(q):
+            want.append(q)
+        q -= 1
+    assert got == want
+    assert cup.primes_below(100, 1000) == [q for q in range(99, 1, -1) if _trial_prime(q)]
+    assert cup.primes_below(2, 5) == []
+
+
+def test_crt_symmetric_range(lib_path):
+    """Host Chinese remaindering (mixed radix): every x in (-M/2, M/2] comes back
+    from its residues, including both ends of the range and zero."""
+    import random
+
+    import paper_1112_5717_gb300 as cup
+    rnd = random.Random(5)
+    for K in (1, 2, 7, 40):
+        primes = cup.primes_below((1 << 31) - rnd.randrange(1 << 20), K)
+        M = 1
+        for q in primes:
+            M *= q
+        cases = [0, 1, -1, (M - 1) // 2, -((M - 1) // 2)] + [rnd.randrange(-(M // 2), M // 2) for _ in range(20)]
+        for x in cases:
+            assert cup.crt([x % q for q in primes], primes) == x
+    small = [5, 7, 11]
+    for x in range(-192, 193):                    # M = 385: all of (-M/2, M/2]
+        assert cup.crt([x % q for q in small], small) == x
+
+
+def test_crt_rejects_bad_primes(lib_path):
+    import paper_1112_5717_gb300 as cup
+    with pytest.raises(cup.CupError) as e:
+        cup.crt([1, 2], [65521, 65521])
+    assert e.value.status == -1
+    with pytest.raises(cup.CupError) as e:
+        cup.crt([1, 2], [65521, 65522])
+    assert e.value.status == -2
+    lib = cup.load()
+    r = (ctypes.c_uint32 * 3)(1, 2, 3)
+    q = (ctypes.c_uint32 * 3)(*cup.primes_below(1 << 31, 3))
+    w = (ctypes.c_uint32 * 1)()
+    nw, sg = ctypes.c_int64(0), ctypes.c_int(0)
+    assert lib.cup_crt(r, q, 3, w, 1, ctypes.byref(nw), ctypes.byref(sg)) == -8
+    assert nw.value >= 2

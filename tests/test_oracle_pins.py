@@ -492,3 +492,72 @@ def test_oracle_inplace_mm_is_the_product(m, n, p):
     assert np.array_equal(oracle.inplace_mm(np.eye(m, dtype=np.int64), B, p).astype(np.int64), B)
     v = rng.integers(0, p, size=(n, 1))
     assert np.array_equal(exact_matmul_mod(got, v, p), exact_matmul_mod(A, exact_matmul_mod(B, v, p), p))
+
+
+def _int_leibniz(M) -> int:
+    n = len(M)
+    total = 0
+    for perm in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if perm[i] > perm[j])
+        prod = 1
+        for i in range(n):
+            prod *= int(M[i][perm[i]])
+        total += -prod if inv & 1 else prod
+    return total
+
+
+def test_oracle_int_det_against_leibniz():
+    """Bareiss det over Z: every 3x3 matrix with entries in {-1, 0, 1} and random
+    5x5 matrices with large signed entries, against the Leibniz formula."""
+    for vals in itertools.product((-1, 0, 1), repeat=9):
+        M = np.array(vals, dtype=np.int64).reshape(3, 3)
+        assert oracle.int_det(M) == _int_leibniz(M)
+    rng = np.random.default_rng(17)
+    for n in (1, 2, 4, 5):
+        for _ in range(5):
+            M = rng.integers(-(1 << 40), 1 << 40, size=(n, n))
+            assert oracle.int_det(M) == _int_leibniz(M)
+
+
+def test_oracle_int_det_closed_forms():
+    """det(L D U) = product of D for unit triangular L, U; Vandermonde =
+    product of node differences; det(A B) = det A det B."""
+    rng = np.random.default_rng(3)
+    n = 14
+    L = np.tril(rng.integers(-3, 4, size=(n, n)), -1) + np.eye(n, dtype=np.int64)
+    U = np.triu(rng.integers(-3, 4, size=(n, n)), 1) + np.eye(n, dtype=np.int64)
+    d = [int(x) for x in rng.integers(1, 9, size=n) * rng.choice([-1, 1], size=n)]
+    A = L.astype(object).dot(np.diag(d).astype(object)).dot(U.astype(object))
+    want = 1
+    for x in d:
+        want *= x
+    assert oracle.int_det(A) == want
+    x = [3, -1, 4, 10, -7, 2]
+    V = np.array([[xi ** j for j in range(len(x))] for xi in x], dtype=object)
+    vd = 1
+    for i in range(len(x)):
+        for j in range(i + 1, len(x)):
+            vd *= x[j] - x[i]
+    assert oracle.int_det(V) == vd
+    B = rng.integers(-50, 50, size=(7, 7))
+    C = rng.integers(-50, 50, size=(7, 7))
+    assert oracle.int_det(B.astype(object).dot(C.astype(object))) == oracle.int_det(B) * oracle.int_det(C)
+
+
+def test_oracle_int_rank_against_minors():
+    """Rank over Q: the largest k with a nonzero k x k minor, by brute force on
+    small matrices, and r for products of random m x r and r x n factors."""
+    rng = np.random.default_rng(8)
+    for _ in range(40):
+        m, n = rng.integers(1, 5, size=2)
+        M = rng.integers(-1, 2, size=(m, n)) * (rng.random((m, n)) < 0.6)
+        best = 0
+        for k in range(1, min(m, n) + 1):
+            for rows in itertools.combinations(range(m), k):
+                for cols in itertools.combinations(range(n), k):
+                    if _int_leibniz(M[np.ix_(rows, cols)]) != 0:
+                        best = k
+        assert oracle.int_rank(M) == best
+    X = rng.integers(-9, 10, size=(12, 4)).astype(object)
+    Y = rng.integers(-9, 10, size=(4, 10)).astype(object)
+    assert oracle.int_rank(X.dot(Y)) == min(4, oracle.int_rank(X), oracle.int_rank(Y))
