@@ -62,6 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--leaf-rows", type=int, default=None)
     ap.add_argument("--window", type=int, default=None)
     ap.add_argument("--tc-min-k", type=int, default=None)
+    ap.add_argument("--int-path", type=int, default=None, choices=[0, 1, 2],
+                    help="int_det images: 0 cost model, 1 batched launch, 2 one CUP per prime")
     ap.add_argument("--profile", type=int, default=0,
                     help="library timing level during the timed steps (0: none, CUDA-graph replay; "
                          "2: every kernel class)")
@@ -174,7 +176,7 @@ def make_workload(args):
     from paper_1112_5717_gb300 import inputs
     w = args.workload
     if w == "dense_full":
-        n = args.n or 8192
+        n = args.n or (512 if args.op == "int_det" else 8192)
         p = args.p or inputs.P_16
         return f"dense_full {n}x{n} uniform over GF({p})", [(inputs.dense_full(n=n, p=p), p)]
     if w == "dense_plain":
@@ -199,12 +201,16 @@ def make_workload(args):
 # Operations and their leading-term operation counts (Table 1, omega = 3): CUP, PLE and
 # det cost 2mnr - (m+n) r^2 + 2/3 r^3; the reduced echelon transform (inverse, rref,
 # nullspace) of a nonsingular n x n matrix costs 2 n^3.
-OPS = ("factor", "ple", "det", "inverse", "rref", "nullspace", "trlum", "inplace_mm")
+OPS = ("factor", "ple", "det", "inverse", "rref", "nullspace", "trlum", "inplace_mm", "int_det")
+_INT_K = [0]      # primes used by the last int_det call
 
 
 def op_ops(op: str, m: int, n: int, r: int) -> float:
     if op in ("factor", "ple", "det"):
         return cup_ops(m, n, r)
+    if op == "int_det":
+        # one CUP per prime image
+        return _INT_K[0] * cup_ops(m, n, r)
     if m != n or r != n:
         raise SystemExit(f"--op {op} needs a square nonsingular workload")
     if op == "trlum":
@@ -216,6 +222,8 @@ def op_ops(op: str, m: int, n: int, r: int) -> float:
 
 
 def op_metric(op: str) -> str:
+    if op == "int_det":
+        return "int_det over Z by CUP modulo primes + CRT, Gop/s (Table 1 leading term, summed over the prime images)"
     return METRIC if op == "factor" else f"{op} over GF(p) Gop/s (Table 1 leading term)"
 
 
@@ -236,6 +244,12 @@ def run_op(h, op: str, A, p: int):
     if op == "trlum":
         h.trlum(A, p)
         return A.shape[0]
+    if op == "int_det":
+        _, r, cert, k = h.int_det(A)
+        if not cert:
+            raise SystemExit("int_det: the bound was not met")
+        _INT_K[0] = k
+        return r
     if op == "inplace_mm":
         # B <- A B with B a device copy of A, made inside the call
         B = _op_scratch(A)
@@ -297,6 +311,20 @@ def oracle_sample(n: int, p: int, workload: str = "dense_full", op: str = "facto
         desc = f"CUP of one {n}x{n} uniform matrix over GF({p}) (the workload scaled down)"
     if op != "factor":
         desc = desc.replace("CUP", op, 1)
+    if op == "int_det":
+        # the same per-image work: CUP modulo each of 4 primes near 2^30 of a centred matrix
+        import numpy as np
+        A = mats[0][0]
+        q0 = int(mats[0][1])
+        Z = A.astype(np.int64) - q0 // 2
+        qs = inputs.primes_below(1 << 30, 4)
+        t0 = time.perf_counter()
+        for q in qs:
+            oracle.det((Z % q).astype(np.uint32), q)
+        dt = time.perf_counter() - t0
+        ops = len(qs) * cup_ops(A.shape[0], A.shape[1], min(A.shape))
+        return (ops / dt / 1e9, dt, oracle.num_threads(),
+                f"det modulo 4 primes near 2^30 of one {A.shape[0]}x{A.shape[1]} centred integer matrix")
     t0 = time.perf_counter()
     ops = 0.0
     for A, q in mats:
@@ -356,13 +384,18 @@ def run_ours(args):
     batched = args.workload == "batched"
 
     # pristine inputs resident in HBM (and pinned host copies for the end-to-end leg)
-    hosts = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).pin_memory()
-             for A, _ in mats]
+    if args.op == "int_det":
+        # the integer matrix: the residues centred around zero, int64
+        hosts = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.int64) - int(q) // 2).pin_memory()
+                 for A, q in mats]
+    else:
+        hosts = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).pin_memory()
+                 for A, _ in mats]
     primes = [int(q) for _, q in mats]
     pristine = [t.to(dev) for t in hosts]
     work = [torch.empty_like(t) for t in pristine]
     opts = {k: v for k, v in (("leaf_rows", args.leaf_rows), ("window", args.window),
-                              ("tc_min_k", args.tc_min_k)) if v is not None}
+                              ("tc_min_k", args.tc_min_k), ("int_path", args.int_path)) if v is not None}
     h = cup.Handle(dev, engine=engine, profile=args.profile, **opts)
     # a stream of our own (calls repeated on it may be replayed as CUDA graphs)
     stream = torch.cuda.Stream()
@@ -438,7 +471,8 @@ def run_ours(args):
                                                     f", {args.op} through the library (CUP, Algorithms 5 and 7-9 or Sec. 5), "
                                                     f"{args.engine} Schur updates")),
                               "engine": args.engine, "leading_term_ops": ops,
-                              "limbs": cup_limbs(primes[0]) if engine == cup.ENGINE_TENSOR else None,
+                              "limbs": (cup_limbs(primes[0]) if args.op != "int_det" else 4)
+                                       if engine == cup.ENGINE_TENSOR else None,
                               "l2": "inputs restored by a device copy before each step; "
                                     "the 256 MiB 8192^2 input exceeds the 129 MiB L2",
                               "parallelism": "replicas" if world > 1 else "single", "options": opts,
@@ -497,7 +531,7 @@ def run_ours(args):
             if i > 0:
                 e2e_ms.append(e0.elapsed_time(e1))
         e_ms = max_over_ranks(statistics.mean(e2e_ms), world)
-        nbytes = sum(t.numel() * 4 for t in hosts)
+        nbytes = sum(t.numel() * t.element_size() for t in hosts)
         result["e2e"] = {"value": ops * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e_ms,
                          "h2d_bytes_per_step": int(nbytes),
                          "d2h_bytes_per_step": int(nbytes + (res_h.numel() * 8 if batched else 0))}

@@ -65,9 +65,11 @@ enum {
     CUP_OPT_TC_MIN_K = 3,      /* smallest inner dimension sent to the tensor engine (default 64) */
     CUP_OPT_VALIDATE = 4,      /* nonzero: check inputs are canonical residues (slow) */
     CUP_OPT_PROFILE = 5,       /* 1: time every Schur-update launch with CUDA events; 2: every launch */
-    CUP_OPT_SCHEDULE = 6       /* cup_factor schedule: 1 (default) device-resident, replayed as a CUDA
+    CUP_OPT_SCHEDULE = 6,      /* cup_factor schedule: 1 (default) device-resident, replayed as a CUDA
                                   graph when a call repeats; 2 device-resident without graphs; 0 host-driven
                                   (reads each block's rank back before launching the next) */
+    CUP_OPT_INT_PATH = 7       /* images of cup_int_det / cup_int_rank: 0 (default) by a cost model,
+                                  1 the batched launch (min(m, n) <= 2048), 2 one full-device CUP per prime */
 };
 
 /* Counters of the work a handle has enqueued since the last cup_reset_stats.

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libcup_gb300.so")
 ENGINE_PLAIN = 0
 ENGINE_TENSOR = 1
 OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE, OPT_PROFILE, OPT_SCHEDULE = 0, 1, 2, 3, 4, 5, 6
+OPT_INT_PATH = 7
 
 
 class Stats(ctypes.Structure):
@@ -178,7 +179,8 @@ class Handle:
         if engine is not None:
             self.set_option(OPT_ENGINE, engine)
         names = {"leaf_rows": OPT_LEAF_ROWS, "window": OPT_WINDOW, "tc_min_k": OPT_TC_MIN_K,
-                 "validate": OPT_VALIDATE, "profile": OPT_PROFILE, "schedule": OPT_SCHEDULE}
+                 "validate": OPT_VALIDATE, "profile": OPT_PROFILE, "schedule": OPT_SCHEDULE,
+                 "int_path": OPT_INT_PATH}
         for k, v in opts.items():
             self.set_option(names[k], int(v))
 

@@ -43,6 +43,7 @@ struct cup_handle {
     size_t ws_bytes = 0;
     int profile = 0;
     int schedule = 1;              // 0: host-driven recursion, 1: device-resident (+ graph replay)
+    int int_path = 0;              // multi-modular images: 0 cost model, 1 batched launch, 2 per prime
     int use_graph = 1;
     int64_t *d_rank_at = nullptr;  // device-resident schedule: rank before each leaf
     int64_t rank_at_cap = 0;
@@ -931,6 +932,10 @@ cup_status cup_set_option(cup_handle *h, int option, int64_t value)
         h->schedule = value ? 1 : 0;
         h->use_graph = value == 1;
         return CUP_OK;
+    case CUP_OPT_INT_PATH:
+        if (value < 0 || value > 2) return CUP_ERR_ARG;
+        h->int_path = (int)value;
+        return CUP_OK;
     default:
         return CUP_ERR_ARG;
     }
@@ -1421,8 +1426,6 @@ cup_status cup_factor_batched(cup_handle *h, const cup_batch_item *d_items, int6
 
 namespace {
 
-const int64_t INT_BATCH_MAX = 512;   // images of this size or less are factored together in one launch
-
 // log2 of the product of the Euclidean norms of the nonzero rows of A: a bound
 // on |det A| (Hadamard) and on every minor of A.
 cup_status int_bound(cup_handle *h, const int64_t *A, int64_t m, int64_t n, int64_t lda, double *out, cudaStream_t st)
@@ -1487,12 +1490,25 @@ cup_status int_residues(cup_handle *h, const int64_t *A, int64_t m, int64_t n, i
 {
     const int64_t K = (int64_t)pr.size();
     const int64_t kmn = m < n ? m : n;
-    const int64_t mx = m > n ? m : n;
     const size_t plane = (size_t)m * (size_t)n;
     uint32_t *d_pr = nullptr;
     CU(cudaMalloc(&d_pr, (size_t)K * sizeof(uint32_t)));
     cup_status s = cuda_ok(h, cudaMemcpyAsync(d_pr, pr.data(), (size_t)K * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    const bool batched = kmn <= INT_BATCH_MAX && mx <= 2048 && (double)K * (double)plane * 4.0 <= 4.0 * (1ull << 30);
+    // Cost model (GB300 measurements): the batched launch runs two images per SM at
+    // about 2.3 G field ops/s each; one full-device CUP per prime runs at about
+    // 450 G ops/s at 1024^2 plus about a millisecond of launches and syncs.
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+    const double ops = 2.0 * (double)m * n * kmn - (double)(m + n) * kmn * kmn + 2.0 / 3.0 * (double)kmn * kmn * kmn;
+    const double waves = std::ceil((double)K / (2.0 * nsm));
+    const double t_batch = waves * ops / 2.3e9;
+    const double t_seq = (double)K * (ops / 4.5e11 + 1.0e-3);
+    const bool fits = kmn <= 2048 && (double)K * (double)plane * 4.0 <= 64.0 * (1ull << 30);
+    const bool batched = fits && (h->int_path == 1 || (h->int_path == 0 && t_batch < t_seq));
+    if (h->int_path == 1 && !fits) {
+        cudaFree(d_pr);
+        return CUP_ERR_UNSUPPORTED;
+    }
     if (s == CUP_OK && batched) {
         // one allocation: residue planes | profile+ipiv per image | items | ranks | dets
         const size_t b_res = (size_t)K * plane * 4, b_idx = (size_t)K * 2 * (size_t)kmn * 8,

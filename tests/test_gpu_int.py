@@ -124,3 +124,18 @@ def test_int_rank_large(handle, m, n, r):
     assert oracle.cup((A % q).astype(np.uint32), q)["rank"] == r
     rank, cert, k = handle.int_rank(_dev64(A))
     assert cert and rank == r
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_int_paths_agree(cuda_lib, path):
+    """The batched launch and the per-prime factorisations give the same results."""
+    h = cuda_lib.Handle(int_path=path)
+    rng = np.random.default_rng(path)
+    A, want = _ldu(rng, 150)
+    det, rank, cert, _ = h.int_det(_dev64(A))
+    assert cert and det == want and rank == 150
+    X = rng.integers(-4, 5, size=(90, 40))
+    Y = rng.integers(-4, 5, size=(40, 120))
+    B = X @ Y
+    assert h.int_rank(_dev64(B))[:2] == (oracle.int_rank(B), True)
+    h.close()
