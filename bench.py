@@ -62,6 +62,9 @@ def parse_args(argv=None):
     ap.add_argument("--leaf-rows", type=int, default=None)
     ap.add_argument("--window", type=int, default=None)
     ap.add_argument("--tc-min-k", type=int, default=None)
+    ap.add_argument("--schedule", type=int, default=None, choices=[0, 1, 2],
+                    help="cup_factor schedule: 1 device-resident replayed as a CUDA graph (default), "
+                         "2 device-resident eager, 0 host-driven")
     ap.add_argument("--int-path", type=int, default=None, choices=[0, 1, 2],
                     help="int_det images: 0 cost model, 1 batched launch, 2 one CUP per prime")
     ap.add_argument("--profile", type=int, default=0,
@@ -395,7 +398,8 @@ def run_ours(args):
     pristine = [t.to(dev) for t in hosts]
     work = [torch.empty_like(t) for t in pristine]
     opts = {k: v for k, v in (("leaf_rows", args.leaf_rows), ("window", args.window),
-                              ("tc_min_k", args.tc_min_k), ("int_path", args.int_path)) if v is not None}
+                              ("tc_min_k", args.tc_min_k), ("int_path", args.int_path),
+                              ("schedule", args.schedule)) if v is not None}
     h = cup.Handle(dev, engine=engine, profile=args.profile, **opts)
     # a stream of our own (calls repeated on it may be replayed as CUDA graphs)
     stream = torch.cuda.Stream()

@@ -161,7 +161,8 @@ def test_factor_tensor_engine(cuda_lib, name, tc_min_k):
 
 
 @pytest.mark.parametrize("schedule", [0, 1, 2])
-@pytest.mark.parametrize("name", ["dense_plain_512", "rank_def_700x256", "tall_500x90_p3", "zero_40x50"])
+@pytest.mark.parametrize("name", ["dense_plain_512", "rank_def_700x256", "tall_500x90_p3", "zero_40x50",
+                                  "wide_90x500_p2", "p31", "one_row"])
 def test_factor_schedules_and_graph_replay(cuda_lib, schedule, name):
     """Host-driven (0), device-resident replayed as a CUDA graph (1) and
     device-resident eager (2): three calls on the same buffer each match the oracle."""
