@@ -320,10 +320,11 @@ k_trsm_ruu128(const TriDesc d, ModP M)
             for (int k = 30; k >= 0; --k) {
                 if (k < nbr) {
                     const uint32_t *uk = sU + (b0 + k) * RUU_LDS + b0;
-                    uint64_t sum = 0;
+                    // four partial sums: the chain of 64-bit adds is a quarter as long
+                    uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-                    for (int l = k + 1; l < 32; ++l) sum += (uint64_t)uk[l] * v[l];
-                    const uint32_t r = red39(sum, M.p, c24, mu32);
+                    for (int l = k + 1; l < 32; ++l) s4[l & 3] += (uint64_t)uk[l] * v[l];
+                    const uint32_t r = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
                     if (k < lane) v[k] = r ? M.p - r : 0u;
                 }
             }
@@ -352,10 +353,10 @@ k_trsm_ruu128(const TriDesc d, ModP M)
                 if (32 * b >= n) break;
                 const uint32_t y = red39(acc[b], M.p, c24, mu32);
                 const uint32_t *V = sV + b * 32 * TRI_VLD + lane;
-                uint64_t sum = 0;
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) sum += (uint64_t)__shfl_sync(0xffffffffu, y, k) * V[k * TRI_VLD];
-                const uint32_t x = red39(sum, M.p, c24, mu32);
+                uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+                for (int k = 0; k < 32; ++k) s4[k & 3] += (uint64_t)__shfl_sync(0xffffffffu, y, k) * V[k * TRI_VLD];
+                const uint32_t x = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
                 xo[b] = x;
                 if (b < 3 && 32 * (b + 1) < n) {
                     const uint32_t nx = x ? M.p - x : 0u;
@@ -432,8 +433,10 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    // one wave of CTAs (two fit an SM): every CTA loads the triangle and, for p < 2^16,
+    // inverts its diagonal blocks, so more rows per CTA spread that fixed cost
     int64_t nb = (d.rows + 7) / 8;
-    if (nb > 152 * 8) nb = 152 * 8;
+    if (nb > 152 * 2) nb = 152 * 2;
     if (M.p < (1u << 16)) k_trsm_ruu128<3><<<(unsigned)nb, 256, smem, st>>>(d, M);
     else if (M.p < (1u << 24)) k_trsm_ruu128<1><<<(unsigned)nb, 256, smem, st>>>(d, M);
     else k_trsm_ruu128<0><<<(unsigned)nb, 256, smem, st>>>(d, M);
