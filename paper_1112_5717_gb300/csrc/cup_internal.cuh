@@ -42,6 +42,37 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 #endif
 
+#ifdef __CUDACC__
+// Programmatic dependent launch. The kernels of the factorisation's launch chain
+// are launched with launch_pdl, so each may become resident while the previous
+// kernel of its stream is still running; every one of them starts with
+// pdl_enter(), which waits for that kernel's completion and memory (nothing is
+// read before it) and then lets the next kernel of the stream be launched. A
+// kernel launched the ordinary way passes both instructions at once.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 static inline Dyn dconst(int64_t v) { return Dyn{v, nullptr, nullptr, 0, 0, v, v}; }
 static inline Dyn dvar(int64_t s, const int64_t *p0, int64_t c0, const int64_t *p1, int64_t c1, int64_t lo,
                        int64_t hi)

@@ -99,6 +99,7 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
               int64_t n, int wn, int speculate, ModP M, SlabScratch *__restrict__ S,
               int64_t *__restrict__ g_ipiv, int64_t *__restrict__ g_prof, int64_t *__restrict__ rank_next)
 {
+    pdl_enter();
     const int64_t col0 = col0d.eval();
     const int64_t w = n - col0;
     if (w <= 0) {
@@ -532,6 +533,7 @@ __global__ void __launch_bounds__(256)
 k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d, int64_t n, ModP M,
               SlabScratch *__restrict__ S, int *__restrict__ err, uint64_t off)
 {
+    pdl_enter();
     constexpr bool WIDE = MODE == 1;
     constexpr int TCL = MODE >= 2 ? MODE - 1 : 0;
     constexpr int TL = TCL > 0 ? TCL : 1;            // array extent for the digit code
@@ -838,6 +840,7 @@ __global__ void __launch_bounds__(256)
 k_laswp_fused(uint32_t *__restrict__ A, int64_t lda, const Dyn row0d, const Dyn nrowsd,
               const int64_t *__restrict__ ipiv, const Dyn k0d, const Dyn k1d)
 {
+    pdl_enter();
     const int64_t row0 = row0d.eval(), nrows = nrowsd.eval();
     const int64_t k0 = k0d.eval(), k1 = k1d.eval();
     if (k1 <= k0 || nrows <= 0 || (int64_t)blockIdx.x * blockDim.x >= nrows) return;
@@ -1021,14 +1024,14 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
     const bool wide = pm1 * pm1 > ~0ull / (uint64_t)(PIV_PB + 1);
     if (M.p & 1u) {
         if (wide)
-            k_slab_pivots<true, true><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S,
-                                                                     ipiv, prof, rank_next);
+            return launch_pdl(k_slab_pivots<true, true>, 1, PIV_THREADS, smem, st, A, lda, a, brows, col0, n, wn,
+                              speculate, M, S, ipiv, prof, rank_next);
         else
-            k_slab_pivots<true, false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S,
-                                                                      ipiv, prof, rank_next);
+            return launch_pdl(k_slab_pivots<true, false>, 1, PIV_THREADS, smem, st, A, lda, a, brows, col0, n, wn,
+                              speculate, M, S, ipiv, prof, rank_next);
     } else {
-        k_slab_pivots<false, false><<<1, PIV_THREADS, smem, st>>>(A, lda, a, brows, col0, n, wn, speculate, M, S,
-                                                                   ipiv, prof, rank_next);
+        return launch_pdl(k_slab_pivots<false, false>, 1, PIV_THREADS, smem, st, A, lda, a, brows, col0, n, wn,
+                          speculate, M, S, ipiv, prof, rank_next);
     }
     return cudaGetLastError();
 }
@@ -1056,9 +1059,9 @@ cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, in
             attr = true;
         }
         SlabScratch *Sm = const_cast<SlabScratch *>(S);
-        if (l == 1) k_slab_finish<2><<<(unsigned)nb, 256, smem, st>>>(A, lda, a, col0, n, M, Sm, err, off);
-        else if (l == 2) k_slab_finish<3><<<(unsigned)nb, 256, smem, st>>>(A, lda, a, col0, n, M, Sm, err, off);
-        else k_slab_finish<4><<<(unsigned)nb, 256, smem, st>>>(A, lda, a, col0, n, M, Sm, err, off);
+        if (l == 1) return launch_pdl(k_slab_finish<2>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
+        if (l == 2) return launch_pdl(k_slab_finish<3>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
+        return launch_pdl(k_slab_finish<4>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
         return cudaGetLastError();
     }
     // a row of Linv times a column of X sums CUP_BMAX products: wide sums unless CUP_BMAX (p-1)^2 < 2^64
@@ -1088,8 +1091,7 @@ cudaError_t launch_laswp_fused(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, co
 {
     if (nrows.hi <= 0 || k1.hi <= k0.lo) return cudaSuccess;
     int64_t nb = (nrows.hi + 255) / 256;
-    k_laswp_fused<<<(unsigned)nb, 256, 0, st>>>(A, lda, row0, nrows, ipiv, k0, k1);
-    return cudaGetLastError();
+    return launch_pdl(k_laswp_fused, (unsigned)nb, 256, 0, st, A, lda, row0, nrows, ipiv, k0, k1);
 }
 
 cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,

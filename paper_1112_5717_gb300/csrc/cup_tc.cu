@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const GemmDesc d, ModP Mp, uint64_t off, uint32_t sh32, int *__restrict__ err)
 {
+    pdl_enter();
     const int M = (int)d.M, N = (int)d.N.eval(), K = (int)d.K.eval();
     const int Kp = (K + BK - 1) / BK * BK;
     const int add = d.add;
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(256)
 k_split(const GemmDesc d, int Kp_stride, int N_stride, int nbA, int gxB, ModP Mp, int mont,
         __nv_bfloat16 *__restrict__ outA, __nv_bfloat16 *__restrict__ outB)
 {
+    pdl_enter();
     __shared__ uint32_t t[32][33];
     const uint32_t p = Mp.p, half = (p - 1) / 2;
     const int K = (int)d.K.eval();
@@ -582,7 +584,9 @@ cudaError_t run_cfg(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t
         const int nbA = (int)((nthr + 255) / 256);
         const int gxB = (Nmax + 31) / 32, gyB = (Kp + 31) / 32;
         const int mont = (L <= 3) && (Mp.p & 1u);
-        k_split<L><<<(unsigned)(nbA + gxB * gyB), 256, 0, st>>>(d, Kp, Nmax, nbA, gxB, Mp, mont, Al, Bl);
+        const cudaError_t e = launch_pdl(k_split<L>, (unsigned)(nbA + gxB * gyB), 256, 0, st, d, Kp, Nmax, nbA, gxB,
+                                         Mp, mont, Al, Bl);
+        if (e != cudaSuccess) return e;
     }
     CUtensorMap ta, tb;
     if (!make_map(&ta, Al, Kp, M, L, BM) || !make_map(&tb, Bl, Kp, Nmax, L, CF::BN))
@@ -599,8 +603,7 @@ cudaError_t run_cfg(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t
     const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
     dim3 grid((Nmax + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
     if (ev0) cudaEventRecord(ev0, st);
-    k_limb_gemm<L, BNX><<<grid, NTHREADS, CF::SMEM, st>>>(ta, tb, d, Mp, off, sh32, err);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_limb_gemm<L, BNX>, grid, NTHREADS, CF::SMEM, st, ta, tb, d, Mp, off, sh32, err);
     if (ev1) cudaEventRecord(ev1, st);
     return e;
 }

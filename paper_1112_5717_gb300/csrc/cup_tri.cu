@@ -260,6 +260,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256)
 k_trsm_ruu128(const TriDesc d, ModP M)
 {
+    pdl_enter();
     constexpr bool MONT = MODE <= 1, LAZY = MODE == 1;
     extern __shared__ __align__(16) uint32_t sU[];        // RUU_MAX x RUU_LDS
     const int n = (int)d.n.eval();
@@ -437,10 +438,9 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
     // inverts its diagonal blocks, so more rows per CTA spread that fixed cost
     int64_t nb = (d.rows + 7) / 8;
     if (nb > 152 * 2) nb = 152 * 2;
-    if (M.p < (1u << 16)) k_trsm_ruu128<3><<<(unsigned)nb, 256, smem, st>>>(d, M);
-    else if (M.p < (1u << 24)) k_trsm_ruu128<1><<<(unsigned)nb, 256, smem, st>>>(d, M);
-    else k_trsm_ruu128<0><<<(unsigned)nb, 256, smem, st>>>(d, M);
-    return cudaGetLastError();
+    if (M.p < (1u << 16)) return launch_pdl(k_trsm_ruu128<3>, (unsigned)nb, 256, smem, st, d, M);
+    if (M.p < (1u << 24)) return launch_pdl(k_trsm_ruu128<1>, (unsigned)nb, 256, smem, st, d, M);
+    return launch_pdl(k_trsm_ruu128<0>, (unsigned)nb, 256, smem, st, d, M);
 }
 
 // ---------------------------------------------------------------------------
