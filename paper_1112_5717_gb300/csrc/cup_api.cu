@@ -591,9 +591,12 @@ cup_status dev_trsm(DevCtx &c, const int64_t *col0p, const int64_t *midp, int64_
     cup_handle *h = c.h;
     if (len <= 0) return CUP_OK;
     if (len <= 128) {
+        // the triangle U1 comes from the top half's finish kernels; the launch just
+        // before this one is the bottom half's transpositions or a TRSM product,
+        // neither of which writes U1 or the ranks
         TriDesc d{c.A, c.lda, dvar(j0, col0p, 1, nullptr, 0, 0, c.n), dvar(j0, col0p, 1, nullptr, 0, 0, c.n),
                   c.A, c.lda, dconst(a2), dvar(j0, col0p, 1, nullptr, 0, 0, c.n), m2,
-                  dvar(-j0, midp, 1, col0p, -1, 0, len)};
+                  dvar(-j0, midp, 1, col0p, -1, 0, len), 1};
         ClassTimer tm(h, c.st, 4);
         CU(launch_trsm_ruu_desc(d, c.M, c.st));
         h->stats.launches += 1;

@@ -54,6 +54,10 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// Data written two or more launches back is complete when a dependent kernel
+// starts (its predecessor passed its own pdl_enter before releasing it), so a
+// prologue that reads only such data may run before pdl_enter; every CTA must
+// still pass pdl_enter before it exits, which keeps the chain ordered.
 #endif
 
 template <typename... KArgs, typename... Args>
@@ -109,6 +113,10 @@ struct TriDesc {
     Dyn brow, bcol;
     int64_t rows;
     Dyn n;
+    // 1: T and the extents were written at least two launches back on the stream
+    // (never by the kernel launched just before), so a kernel launched with
+    // launch_pdl may read them before waiting for its predecessor
+    int pre = 0;
 };
 
 #define CUP_BMAX 64        // most rows a leaf slab may hold

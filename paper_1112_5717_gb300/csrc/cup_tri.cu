@@ -260,11 +260,17 @@ template <int MODE>
 __global__ void __launch_bounds__(256)
 k_trsm_ruu128(const TriDesc d, ModP M)
 {
-    pdl_enter();
+    // the triangle's load and block inverses run before the wait when d.pre says
+    // the triangle and the extents are older than the predecessor kernel
+    const bool pre = d.pre != 0;
+    if (!pre) pdl_enter();
     constexpr bool MONT = MODE <= 1, LAZY = MODE == 1;
     extern __shared__ __align__(16) uint32_t sU[];        // RUU_MAX x RUU_LDS
     const int n = (int)d.n.eval();
-    if (n <= 0) return;
+    if (n <= 0) {
+        if (pre) pdl_enter();
+        return;
+    }
     const int64_t m = d.rows, ldt = d.ldt, ldb = d.ldb;
     const uint32_t *__restrict__ T = d.T + d.trow.eval() * ldt + d.tcol.eval();
     uint32_t *__restrict__ B = d.B + d.brow.eval() * ldb + d.bcol.eval();
@@ -335,6 +341,7 @@ k_trsm_ruu128(const TriDesc d, ModP M)
         }
         __syncthreads();
     }
+    if (pre) pdl_enter();
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nw) {
         uint32_t *row = B + i * ldb;
