@@ -211,13 +211,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const GemmDesc d, ModP Mp, uint64_t off, uint32_t sh32, int *__restrict__ err)
 {
-    pdl_enter();
+    // The launch just before this one is always this product's k_split, so only the
+    // limb planes depend on it: the extents, C and the setup are read or done
+    // before pdl_enter (C and the ranks come from earlier launches).
     const int M = (int)d.M, N = (int)d.N.eval(), K = (int)d.K.eval();
     const int Kp = (K + BK - 1) / BK * BK;
     const int add = d.add;
     const int64_t ldc = d.ldc;
     using CF = Cfg<L, BNX>;
-    if ((int)blockIdx.x * CF::BN >= N || K <= 0) return;       // outside this call's extents
+    if ((int)blockIdx.x * CF::BN >= N || K <= 0) {            // outside this call's extents
+        pdl_enter();
+        return;
+    }
     uint32_t *C = d.C + d.crow.eval() * ldc + d.ccol.eval();
     constexpr int BN = CF::BN, NACC = CF::NACC, NSTAGE = CF::NSTAGE, NBUF = CF::NBUF;
     extern __shared__ uint8_t smem_raw[];
@@ -253,6 +258,19 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // With a short K the epilogue warps copy the C tile asynchronously (coalesced)
+    // into the shared memory the unused stages leave; it lands while the MMAs run.
+    uint32_t *cbuf = (uint32_t *)(smem + CF::SMEMUSE - CF::CBUF);
+    if (pref && warp >= 2) {
+        constexpr int PER = BM * BN / (32 * NEPI);
+        const int et = threadIdx.x - 64;
+#pragma unroll 8
+        for (int i = 0; i < PER; ++i) {
+            const int e = et + 32 * NEPI * i, rr = e / BN, cc = e % BN;
+            if (m0 + rr < M && n0 + cc < N) cp_async4(cbuf + e, C + (int64_t)(m0 + rr) * ldc + n0 + cc);
+        }
+    }
+    pdl_enter();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -326,8 +344,7 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else {
         // ---------------- epilogue warps ----------------
-        // (1) With a short K the C tile is copied asynchronously (coalesced) into
-        // the shared memory the unused stages leave, while the MMAs run.
+        // (1) With a short K the C tile was prefetched into cbuf (above).
         // (2) Per chunk, warp w reads TMEM lane quarter w % 4 (one row per thread)
         // and a quarter of the columns, recombines the shift accumulators in 64 bits and
         // reduces them; partial sums of earlier chunks wait in the TMEM columns
@@ -337,14 +354,6 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // updated with the lanes along the columns.
         const int et = threadIdx.x - 64;                  // 0 .. 32 NEPI - 1
         constexpr int PER = BM * BN / (32 * NEPI);        // C entries per thread
-        uint32_t *cbuf = (uint32_t *)(smem + CF::SMEMUSE - CF::CBUF);
-        if (pref) {
-#pragma unroll 8
-            for (int i = 0; i < PER; ++i) {
-                const int e = et + 32 * NEPI * i, rr = e / BN, cc = e % BN;
-                if (m0 + rr < M && n0 + cc < N) cp_async4(cbuf + e, C + (int64_t)(m0 + rr) * ldc + n0 + cc);
-            }
-        }
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
         const int cg = (warp - 2) >> 2;                   // which quarter of the BN columns
         constexpr int CPW = BN / 4;                       // columns per thread
