@@ -520,19 +520,26 @@ def run_ours(args):
     if not args.no_e2e:
         outs = [torch.empty_like(t).pin_memory() for t in hosts]
         e2e_ms = []
-        for i in range(max(args.steps, 1) + 1):
+        # untimed calls first: the host-buffer call is captured as a graph on its second call
+        e2e_warm = 2 if (args.op == "factor" and not batched) else 1
+        for i in range(max(args.steps, 1) + e2e_warm):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for w_, t in zip(work, hosts):
-                w_.copy_(t, non_blocking=True)
-            res = compute()
-            for o, w_ in zip(outs, work):
-                o.copy_(w_, non_blocking=True)
-            res_h = res.to("cpu", non_blocking=True) if batched else None
+            if args.op == "factor" and not batched:
+                # the library's host-buffer call: row chunks of the input overlap the factorization
+                h.factor_host(hosts[0], work[0], primes[0], out=outs[0])
+                res_h = None
+            else:
+                for w_, t in zip(work, hosts):
+                    w_.copy_(t, non_blocking=True)
+                res = compute()
+                for o, w_ in zip(outs, work):
+                    o.copy_(w_, non_blocking=True)
+                res_h = res.to("cpu", non_blocking=True) if batched else None
             e1.record(stream)
             torch.cuda.synchronize()
-            if i > 0:
+            if i >= e2e_warm:
                 e2e_ms.append(e0.elapsed_time(e1))
         e_ms = max_over_ranks(statistics.mean(e2e_ms), world)
         nbytes = sum(t.numel() * t.element_size() for t in hosts)

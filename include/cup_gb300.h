@@ -124,6 +124,19 @@ cup_status cup_factor(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int
                       uint32_t p, int64_t *d_profile, int64_t *d_ipiv, int64_t *rank,
                       void *stream);
 
+/* cup_factor with the input and the result in HOST memory: hA (m x n, leading
+ * dimension ldh, ideally page-locked) is factored, [C\U] is written to hOut (may
+ * equal hA), and A (DEVICE, m x n, lda) is the working copy, holding [C\U] too on
+ * return; d_profile, d_ipiv and *rank as in cup_factor. The input is copied in row
+ * chunks (one leaf, one leaf, then doubling) on a second stream, and the
+ * factorization waits for a chunk only when it first reaches its rows, so the
+ * copy overlaps the elimination of the rows above it; the copy back starts when
+ * the factorization ends. Repeated calls with the same buffers on a non-default
+ * stream are replayed as one CUDA graph, copies included. Synchronises `stream`. */
+cup_status cup_factor_host(cup_handle *handle, const uint32_t *hA, int64_t ldh, uint32_t *hOut, uint32_t *A,
+                           int64_t m, int64_t n, int64_t lda, uint32_t p, int64_t *d_profile, int64_t *d_ipiv,
+                           int64_t *rank, void *stream);
+
 /*
  * Rank and row rank profile (Sec. 2; Prop. 3). A is destroyed (it receives
  * the [C\U] factors). d_profile as in cup_factor.

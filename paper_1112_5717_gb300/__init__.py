@@ -58,6 +58,7 @@ SIGNATURES = {
     "cup_reset_stats": (_INT, [_P]),
     "cup_class_ms": (_INT, [_P, _P]),
     "cup_factor": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
+    "cup_factor_host": (_INT, [_P, _P, _I64, _P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_rank_profile": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _I64P, _P]),
     "cup_det": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
     "cup_inverse": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
@@ -233,6 +234,31 @@ class Handle:
         st = self.lib.cup_factor(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(),
                                  ipiv.data_ptr(), ctypes.byref(r), _stream_ptr(stream))
         self._check(st, "cup_factor", self.h)
+        return r.value, prof, ipiv
+
+    def factor_host(self, hA, A, p: int, out=None, stream=None):
+        """CUP of a host matrix: hA (CPU int32 tensor, ideally pinned) is copied into the
+        device work tensor A in row chunks that overlap the factorization, and [C\\U]
+        comes back into `out` (default: hA itself). Returns (rank, profile, ipiv)."""
+        torch = _torch()
+        if not isinstance(hA, torch.Tensor) or hA.is_cuda or hA.dtype != torch.int32 or hA.dim() != 2 \
+                or hA.stride(1) != 1:
+            raise TypeError("hA must be a row-major CPU torch.int32 tensor")
+        out = hA if out is None else out
+        if not isinstance(out, torch.Tensor) or out.is_cuda or out.dtype != torch.int32 or out.shape != hA.shape \
+                or out.stride() != hA.stride():
+            raise TypeError("out must be a CPU torch.int32 tensor laid out like hA")
+        m, n, lda = _mat(A, "A")
+        if tuple(hA.shape) != (m, n):
+            raise ValueError("hA and A must have the same shape")
+        k = max(min(m, n), 1)
+        prof = torch.empty(k, dtype=torch.int64, device=A.device)
+        ipiv = torch.empty(k, dtype=torch.int64, device=A.device)
+        r = ctypes.c_int64(0)
+        st = self.lib.cup_factor_host(self.h, hA.data_ptr(), max(hA.stride(0), 1), out.data_ptr(), A.data_ptr(),
+                                      m, n, lda, p, prof.data_ptr(), ipiv.data_ptr(), ctypes.byref(r),
+                                      _stream_ptr(stream))
+        self._check(st, "cup_factor_host", self.h)
         return r.value, prof, ipiv
 
     def rank_profile(self, A, p: int, stream=None):

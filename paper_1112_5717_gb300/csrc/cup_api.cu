@@ -44,6 +44,9 @@ struct cup_handle {
     int profile = 0;
     int schedule = 1;              // 0: host-driven recursion, 1: device-resident (+ graph replay)
     int int_path = 0;              // multi-modular images: 0 cost model, 1 batched launch, 2 per prime
+    cudaStream_t copy = nullptr;   // host-to-device copies of cup_factor_host, overlapping the factorization
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;  // one per row chunk of a host input
     int use_graph = 1;
     int64_t *d_rank_at = nullptr;  // device-resident schedule: rank before each leaf
     int64_t rank_at_cap = 0;
@@ -59,6 +62,8 @@ struct cup_handle {
         bool no_capture;                  // capture failed once: stay eager
         std::vector<int> timed;           // indices into graph_timed, read after each replay
         std::vector<GemmDesc> gemms;      // the Schur updates it runs (extents resolved per replay)
+        const uint32_t *hA = nullptr;     // host input copied in by the graph (cup_factor_host)
+        int64_t ldh = 0;
     };
     int64_t gen = 0;                   // bumped whenever a buffer a graph may reference moves
     std::vector<GraphEntry> graphs;
@@ -536,7 +541,23 @@ struct DevCtx {
     cudaStream_t st;
     int nleaf;
     std::vector<GemmDesc> *gemms;     // every Schur update enqueued (extents resolved after the run)
+    // host input arriving in row chunks: chunk i starts at row chunk_row[i] and has
+    // landed at chunk_ev[i]; rows of chunks before next_chunk are known to be there
+    const int64_t *chunk_row = nullptr;
+    const cudaEvent_t *chunk_ev = nullptr;
+    int nchunk = 0, next_chunk = 0;
 };
+
+// The stream waits for every chunk of a host input that holds a row below y.
+cup_status need_rows(DevCtx &c, int64_t y)
+{
+    cup_handle *h = c.h;
+    while (c.next_chunk < c.nchunk && y > c.chunk_row[c.next_chunk]) {
+        CU(cudaStreamWaitEvent(c.st, c.chunk_ev[c.next_chunk], 0));
+        ++c.next_chunk;
+    }
+    return CUP_OK;
+}
 
 // Host evaluation of a Dyn whose pointers point into the device array dbase,
 // given a host copy hbase of that array.
@@ -618,6 +639,7 @@ cup_status dev_rec(DevCtx &c, int64_t a, int64_t mrows)
     cup_handle *h = c.h;
     if (mrows <= 0) return CUP_OK;
     if (mrows <= h->leaf_rows) {
+        CK(need_rows(c, a + mrows));
         const int L = c.nleaf++;
         const Dyn col0 = dvar(0, c.rank_at + L, 1, nullptr, 0, 0, c.n);
         {
@@ -639,6 +661,7 @@ cup_status dev_rec(DevCtx &c, int64_t a, int64_t mrows)
     const int Lm = c.nleaf;
     const int64_t *col0p = c.rank_at + L0, *midp = c.rank_at + Lm;
     const int64_t a2 = a + k, m2 = mrows - k, kmax = k < c.n ? k : c.n;
+    CK(need_rows(c, a2 + m2));
     // A2 <- A2 P1^T
     CK(dev_laswp(c, dconst(a2), dconst(m2), dvar(0, col0p, 1, nullptr, 0, 0, c.n), dvar(0, midp, 1, nullptr, 0, 0, c.n)));
     // G <- A21 U1^{-1}
@@ -692,8 +715,12 @@ cudaError_t launch_cup_batched(const cup_batch_item *items, int64_t count, int64
 
 namespace {
 
+// hA (host, leading dimension ldh), if given, is the input: it is copied into A in
+// row chunks on a second stream, and the factorization waits for a chunk only
+// when it first touches one of its rows (the recursion reaches the rows in order).
 cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
-                         int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, cudaStream_t st)
+                         int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, cudaStream_t st,
+                         const uint32_t *hA = nullptr, int64_t ldh = 0)
 {
     const int64_t nleaves = count_leaves(m, h->leaf_rows);
     if (nleaves + 1 > h->rank_at_cap) {
@@ -732,7 +759,8 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
     // graph replay for a repeated call with the same buffers and options
     cup_handle::GraphEntry *ge = nullptr;
     for (auto &e : h->graphs)
-        if (e.A == A && e.m == m && e.n == n && e.lda == lda && e.p == p && e.prof == d_profile &&
+        if (e.A == A && e.m == m && e.n == n && e.lda == lda && e.p == p && e.prof == d_profile && e.hA == hA &&
+            e.ldh == ldh &&
             e.ipiv == d_ipiv && e.st == st && e.leaf_rows == h->leaf_rows && e.window == h->window &&
             e.engine == h->engine && e.tc_min_k == h->tc_min_k)
             ge = &e;
@@ -741,13 +769,42 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
         ge->exec = nullptr;
         ge->gen = h->gen;
     }
+    // row chunks of a host input: one leaf, one leaf, then doubling (the first rows
+    // the recursion's leftmost path reaches beyond each split)
+    std::vector<int64_t> chunk_row;
+    if (hA) {
+        for (int64_t r0 = 0, len = h->leaf_rows; r0 < m; r0 += len, len = (r0 > len ? r0 : len))
+            chunk_row.push_back(r0);
+        if (!h->copy) CU(cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
+        if (!h->ev_fork) CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        while (h->chunk_ev.size() < chunk_row.size()) {
+            cudaEvent_t e = nullptr;
+            CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->chunk_ev.push_back(e);
+        }
+    }
     auto enqueue = [&](std::vector<GemmDesc> &gl) -> cup_status {
-        CU(cudaMemcpy2DAsync(h->d_backup, (size_t)n * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m,
-                             cudaMemcpyDeviceToDevice, st));
+        DevCtx c{h, A, lda, m, n, M, d_ipiv, d_profile, h->d_rank_at, st, 0, &gl};
+        if (hA) {
+            CU(cudaEventRecord(h->ev_fork, st));
+            CU(cudaStreamWaitEvent(h->copy, h->ev_fork, 0));
+            for (size_t i = 0; i < chunk_row.size(); ++i) {
+                const int64_t r0 = chunk_row[i], r1 = i + 1 < chunk_row.size() ? chunk_row[i + 1] : m;
+                CU(cudaMemcpy2DAsync(A + r0 * lda, (size_t)lda * 4, hA + r0 * ldh, (size_t)ldh * 4, (size_t)n * 4,
+                                     (size_t)(r1 - r0), cudaMemcpyHostToDevice, h->copy));
+                CU(cudaEventRecord(h->chunk_ev[i], h->copy));
+            }
+            c.chunk_row = chunk_row.data();
+            c.chunk_ev = h->chunk_ev.data();
+            c.nchunk = (int)chunk_row.size();
+        } else {
+            CU(cudaMemcpy2DAsync(h->d_backup, (size_t)n * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m,
+                                 cudaMemcpyDeviceToDevice, st));
+        }
         CU(cudaMemsetAsync(h->d_rank_at, 0, sizeof(int64_t), st));
         CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
-        DevCtx c{h, A, lda, m, n, M, d_ipiv, d_profile, h->d_rank_at, st, 0, &gl};
         CK(dev_rec(c, 0, m));
+        CK(need_rows(c, INT64_MAX));          // every copy joined (a capture needs the copy stream joined)
         CU(cudaMemcpyAsync(h->h_rank, h->d_rank_at, (size_t)(nleaves + 1) * sizeof(int64_t),
                            cudaMemcpyDeviceToHost, st));
         CU(cudaMemcpyAsync(h->h_pinned + 8, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -788,7 +845,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
             h->pending.resize(pend0);
             h->stats.launches = launches0;
             ge->gemms.clear();
-            return factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st);
+            return factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, hA, ldh);
         }
         ge->exec = exec;
         ge->launches = h->stats.launches - launches0;
@@ -806,7 +863,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
         if (!ge && h->use_graph && capturable) {
             // remember the call; the next identical one is captured and replayed
             cup_handle::GraphEntry e{A, m, n, lda, p, d_profile, d_ipiv, st, h->leaf_rows, h->window, h->engine,
-                                     h->tc_min_k, h->gen, nullptr, 0, false, {}, {}};
+                                     h->tc_min_k, h->gen, nullptr, 0, false, {}, {}, hA, ldh};
             if (h->graphs.size() > 16) {
                 if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
                 h->graphs.erase(h->graphs.begin());
@@ -892,6 +949,9 @@ cup_status cup_destroy(cup_handle *h)
         if (h->d_err) cudaFree(h->d_err);
         if (h->d_next) cudaFree(h->d_next);
         if (h->d_ws) cudaFree(h->d_ws);
+        if (h->copy) cudaStreamDestroy(h->copy);
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        for (cudaEvent_t e : h->chunk_ev) cudaEventDestroy(e);
         if (h->d_rank_at) cudaFree(h->d_rank_at);
         if (h->d_backup) cudaFree(h->d_backup);
         if (h->h_rank) cudaFreeHost(h->h_rank);
@@ -997,6 +1057,37 @@ cup_status cup_factor(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t 
     CK(check_device_error(h, c.st));
     *rank = r;
     return CUP_OK;
+}
+
+cup_status cup_factor_host(cup_handle *h, const uint32_t *hA, int64_t ldh, uint32_t *hOut, uint32_t *A, int64_t m,
+                           int64_t n, int64_t lda, uint32_t p, int64_t *d_profile, int64_t *d_ipiv, int64_t *rank,
+                           void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1) || ldh < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_prime(p));
+    *rank = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!hA || !hOut || !A || !d_profile || !d_ipiv) return CUP_ERR_ARG;
+    if (n >= (int64_t)1 << 31) return CUP_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t wb = (size_t)n * 4;
+    cup_status s = CUP_ERR_SPECULATION_INTERNAL;
+    if (h->schedule == 1) s = factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, hA, ldh);
+    if (s == CUP_ERR_SPECULATION_INTERNAL) {
+        // host-driven schedule, or a row taken as dependent was not: redo exactly from the host input
+        CU(cudaMemcpy2DAsync(A, (size_t)lda * 4, hA, (size_t)ldh * 4, wb, (size_t)m, cudaMemcpyHostToDevice, st));
+        Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, st};
+        int64_t r = 0;
+        CK(cup_rec(c, 0, m, 0, &r));
+        CK(check_device_error(h, st));
+        *rank = r;
+        s = CUP_OK;
+    }
+    CK(s);
+    CU(cudaMemcpy2DAsync(hOut, (size_t)ldh * 4, A, (size_t)lda * 4, wb, (size_t)m, cudaMemcpyDeviceToHost, st));
+    return sync_stream(h, st);
 }
 
 cup_status cup_rank_profile(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda,

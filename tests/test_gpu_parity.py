@@ -194,3 +194,50 @@ def test_speculation_fallback_is_exact(cuda_lib):
     A = _swappy(200, 210, p, seed=77)
     for window in (1, 2, 4):
         _factor_case(cuda_lib, A, p, engine=1, leaf_rows=16, window=window, schedule=1)
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+@pytest.mark.parametrize("name", ["dense_plain_512", "rank_def_700x256", "tall_500x90_p3", "wide_90x500_p2",
+                                  "p31", "one_row", "zero_40x50"])
+@pytest.mark.parametrize("pinned,inplace", [(True, False), (True, True), (False, False)])
+def test_factor_host_buffers(cuda_lib, schedule, name, pinned, inplace):
+    """cup_factor_host: the host input arrives in row chunks that overlap the
+    factorization; three calls on the same buffers (replayed as a CUDA graph on a
+    stream of our own) each return the oracle's [C\\U] in host memory."""
+    import torch
+    A, p = FACTOR_CASES[name]()
+    d = oracle.cup_packed(A, p)
+    h = cuda_lib.Handle(engine=1, schedule=schedule)
+    src = torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32))
+    hA = src.clone().pin_memory() if pinned else src.clone()
+    out = hA if inplace else (torch.empty_like(hA).pin_memory() if pinned else torch.empty_like(hA))
+    dA = torch.empty(A.shape, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    for call in range(3):
+        if inplace:
+            hA.copy_(src)
+        with torch.cuda.stream(stream):
+            r, prof, ipiv = h.factor_host(hA, dA, p, out=out)
+        torch.cuda.synchronize()
+        assert r == d["rank"], call
+        assert np.array_equal(prof[:r].cpu().numpy(), d["profile"]), call
+        assert np.array_equal(ipiv[:r].cpu().numpy(), d["ipiv"]), call
+        assert np.array_equal(out.numpy().view(np.uint32).astype(np.int64), d["packed"]), call
+        assert np.array_equal(_host(dA), d["packed"]), call
+    h.close()
+
+
+def test_factor_host_speculation_fallback(cuda_lib):
+    """A window of one position makes rows be taken as dependent that are not; the
+    host-buffer call redoes the factorization from the host input and stays exact."""
+    import torch
+    p = 251
+    A = _swappy(200, 210, p, seed=77)
+    d = oracle.cup_packed(A, p)
+    h = cuda_lib.Handle(engine=1, leaf_rows=16, window=1)
+    hA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).clone().pin_memory()
+    dA = torch.empty(A.shape, dtype=torch.int32, device="cuda")
+    r, prof, ipiv = h.factor_host(hA, dA, p)
+    assert r == d["rank"]
+    assert np.array_equal(hA.numpy().view(np.uint32).astype(np.int64), d["packed"])
+    h.close()
