@@ -550,6 +550,15 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
     const int ext_pos = S->ext_pos, ext_slot = S->ext_slot;
+    if (TCL > 0 && q0 == 0) {
+        // the first tile also writes the slab's C values (positions < r_s <= CUP_QT);
+        // the tensor-core product leaves sL unused, so their copy into it starts now
+        // and lands while the product runs
+        for (int idx = tid; idx < CUP_BMAX * CUP_BMAX; idx += nt) {
+            const int i = idx >> 6, t = idx & 63;
+            if (i < stop && t < rs) cp_async4(&sL[i][t], &S->Cn[i][t]);
+        }
+    }
 
     for (int t = tid; t < rs; t += nt) { sProf[t] = S->prof[t]; sPinv[t] = S->pinv[t]; }
     for (int qq = tid; qq < nq; qq += nt) {
@@ -727,8 +736,10 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
             if (err) atomicCAS(err, 0, CUP_DEVERR_SPECULATION);
         }
     }
-    // C values for the first tile (positions < r_s <= CUP_QT): sL is free again
-    if (q0 == 0) {
+    // C values for the first tile: already in sL with tensor-core digits, else read now
+    // (sL is free again after the CUDA-core product)
+    if (TCL > 0 && q0 == 0) cp_async_wait_all();
+    if (TCL == 0 && q0 == 0) {
         __syncthreads();
         const int t = tid & 63, i0 = tid >> 6;
         uint32_t cv[16];
@@ -849,6 +860,13 @@ k_laswp_fused(uint32_t *__restrict__ A, int64_t lda, const Dyn row0d, const Dyn 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
     uint32_t *row = A + (row0 + i) * lda;
+    {
+        // usually every transposition of the range is trivial: check the whole range
+        // with independent loads (one memory latency) before the ordered pass
+        bool any = false;
+        for (int64_t t = k0 + tid; t < k1; t += blockDim.x) any |= ipiv[t] != t;
+        if (!__syncthreads_or(any)) return;
+    }
     for (int64_t c0 = k0; c0 < k1; c0 += 256) {
         const int64_t t = c0 + tid;
         const int64_t c = (t < k1) ? ipiv[t] : t;
