@@ -949,6 +949,7 @@ template <bool WIDE>
 __global__ void __launch_bounds__(256)
 k_gemm_sub_cc(const GemmDesc d, ModP Mp)
 {
+    pdl_enter();
     const int64_t Mr = d.M, N = d.N.eval(), K = d.K.eval();
     if ((int64_t)blockIdx.x * GB_N >= N || K <= 0) return;
     const int add = d.add;
@@ -1132,9 +1133,9 @@ cudaError_t launch_gemm_cc_desc(const GemmDesc &d, ModP M, cudaStream_t st)
     // K (p-1)^2 < 2^64 means the 64-bit sum of products cannot wrap
     long double bound = (long double)d.K.hi * (long double)(M.p - 1) * (long double)(M.p - 1);
     if (bound < 18446744073709551615.0L)
-        k_gemm_sub_cc<false><<<grid, 256, 0, st>>>(d, M);
+        launch_pdl(k_gemm_sub_cc<false>, grid, 256, 0, st, d, M);
     else
-        k_gemm_sub_cc<true><<<grid, 256, 0, st>>>(d, M);
+        launch_pdl(k_gemm_sub_cc<true>, grid, 256, 0, st, d, M);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ template <bool UPPER, bool UNIT, bool SOLVE, bool MONT>
 __global__ void __launch_bounds__(256)
 k_tri_right(const TriDesc d, ModP M)
 {
+    pdl_enter();
     const int n = (int)d.n.eval();
     if (n <= 0) return;
     const int64_t m = d.rows, ldt = d.ldt, ldb = d.ldb;
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(256)
 k_tri_left(const uint32_t *__restrict__ T, int64_t ldt, uint32_t *__restrict__ B, int64_t ldb, int n,
            int64_t k, ModP M)
 {
+    pdl_enter();
     __shared__ uint32_t sT[TRI_MAX][TRI_MAX + 1];
     __shared__ uint32_t sD[TRI_MAX];
     __shared__ uint32_t sB[TRI_MAX][TRI_COLS + 1];
@@ -195,14 +197,14 @@ static cudaError_t tri_dispatch(bool left, const uint32_t *T, int64_t ldt, uint3
     const bool mont = (M.p & 1u) != 0;
     if (left) {
         const int64_t nb = (cols + TRI_COLS - 1) / TRI_COLS;
-        if (mont) k_tri_left<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, n, cols, M);
-        else k_tri_left<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, 256, 0, st>>>(T, ldt, B, ldb, n, cols, M);
+        if (mont) launch_pdl(k_tri_left<UPPER, UNIT, SOLVE, true>, (unsigned)nb, 256, 0, st, T, ldt, B, ldb, n, cols, M);
+        else launch_pdl(k_tri_left<UPPER, UNIT, SOLVE, false>, (unsigned)nb, 256, 0, st, T, ldt, B, ldb, n, cols, M);
     } else {
         int64_t nb = (rows + 7) / 8;
         if (nb > 152 * 16) nb = 152 * 16;
         TriDesc d{T, ldt, dconst(0), dconst(0), B, ldb, dconst(0), dconst(0), rows, dconst(n)};
-        if (mont) k_tri_right<UPPER, UNIT, SOLVE, true><<<(unsigned)nb, 256, 0, st>>>(d, M);
-        else k_tri_right<UPPER, UNIT, SOLVE, false><<<(unsigned)nb, 256, 0, st>>>(d, M);
+        if (mont) launch_pdl(k_tri_right<UPPER, UNIT, SOLVE, true>, (unsigned)nb, 256, 0, st, d, M);
+        else launch_pdl(k_tri_right<UPPER, UNIT, SOLVE, false>, (unsigned)nb, 256, 0, st, d, M);
     }
     return cudaGetLastError();
 }
@@ -455,6 +457,7 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
 // ---------------------------------------------------------------------------
 __global__ void k_negate(uint32_t *__restrict__ B, int64_t ldb, int64_t m, int64_t n, uint32_t p)
 {
+    pdl_enter();
     const int64_t total = m * n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -469,7 +472,7 @@ cudaError_t launch_negate(uint32_t *B, int64_t ldb, int64_t m, int64_t n, uint32
     if (m <= 0 || n <= 0) return cudaSuccess;
     int64_t nb = (m * n + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_negate<<<(unsigned)nb, 256, 0, st>>>(B, ldb, m, n, p);
+    launch_pdl(k_negate, (unsigned)nb, 256, 0, st, B, ldb, m, n, p);
     return cudaGetLastError();
 }
 
@@ -482,6 +485,7 @@ __global__ void k_row_swaps(uint32_t *__restrict__ A, int64_t lda, int64_t ncols
                             const int64_t *__restrict__ list, int64_t count, int64_t base_a,
                             int64_t base_b, int reverse, int prefix)
 {
+    pdl_enter();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     for (int64_t s = 0; s < count; ++s) {
@@ -499,7 +503,7 @@ cudaError_t launch_row_swaps(uint32_t *A, int64_t lda, int64_t ncols, const int6
                              int64_t base_a, int64_t base_b, int reverse, int prefix, cudaStream_t st)
 {
     if (ncols <= 0 || count <= 0) return cudaSuccess;
-    k_row_swaps<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(A, lda, ncols, list, count, base_a, base_b,
+    launch_pdl(k_row_swaps, (unsigned)((ncols + 255) / 256), 256, 0, st, A, lda, ncols, list, count, base_a, base_b,
                                                                    reverse, prefix);
     return cudaGetLastError();
 }
@@ -528,6 +532,7 @@ cudaError_t launch_gather_rows(uint32_t *dst, int64_t ldd, const uint32_t *src, 
 // B[i][j] = (diag && i == j) ? 1 : 0 on an m x n block
 __global__ void k_fill(uint32_t *__restrict__ B, int64_t ldb, int64_t m, int64_t n, int diag)
 {
+    pdl_enter();
     const int64_t total = m * n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -541,7 +546,7 @@ cudaError_t launch_fill(uint32_t *B, int64_t ldb, int64_t m, int64_t n, int diag
     if (m <= 0 || n <= 0) return cudaSuccess;
     int64_t nb = (m * n + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_fill<<<(unsigned)nb, 256, 0, st>>>(B, ldb, m, n, diag);
+    launch_pdl(k_fill, (unsigned)nb, 256, 0, st, B, ldb, m, n, diag);
     return cudaGetLastError();
 }
 
@@ -573,6 +578,7 @@ __global__ void __launch_bounds__(256)
 k_transpose(uint32_t *__restrict__ D, int64_t ldd, const uint32_t *__restrict__ S, int64_t lds, int64_t m,
             int64_t n)
 {
+    pdl_enter();
     __shared__ uint32_t t[32][33];
     const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;       // 8 rows of 32
@@ -595,7 +601,7 @@ cudaError_t launch_transpose(uint32_t *D, int64_t ldd, const uint32_t *S, int64_
     if (m <= 0 || n <= 0) return cudaSuccess;
     if ((n + 31) / 32 > 0x7fffffff || (m + 31) / 32 > 65535) return cudaErrorInvalidValue;
     dim3 g((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
-    k_transpose<<<g, 256, 0, st>>>(D, ldd, S, lds, m, n);
+    launch_pdl(k_transpose, g, 256, 0, st, D, ldd, S, lds, m, n);
     return cudaGetLastError();
 }
 
@@ -603,6 +609,7 @@ cudaError_t launch_transpose(uint32_t *D, int64_t ldd, const uint32_t *S, int64_
 __global__ void k_copy(uint32_t *__restrict__ D, int64_t ldd, const uint32_t *__restrict__ S, int64_t lds,
                        int64_t m, int64_t n)
 {
+    pdl_enter();
     const int64_t total = m * n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -617,7 +624,7 @@ cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds
     if (m <= 0 || n <= 0) return cudaSuccess;
     int64_t nb = (m * n + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_copy<<<(unsigned)nb, 256, 0, st>>>(D, ldd, S, lds, m, n);
+    launch_pdl(k_copy, (unsigned)nb, 256, 0, st, D, ldd, S, lds, m, n);
     return cudaGetLastError();
 }
 
@@ -629,6 +636,7 @@ template <bool UPPER, bool UNIT, bool MONT>
 __global__ void __launch_bounds__(512)
 k_trtri_leaf(uint32_t *__restrict__ T, int64_t ldt, int n, ModP M)
 {
+    pdl_enter();
     // T^{-1} as the solution of T X = I: sixteen warps, four columns each, lanes along
     // the rows; row i is finalised (divided by its diagonal), broadcast from its lane,
     // and the rows that depend on it subtract t_ki x_i
@@ -684,8 +692,8 @@ cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int
     if (n > TRI_MAX) return cudaErrorInvalidValue;
     const bool mont = (M.p & 1u) != 0;
 #define TRTRI_CASE(U, D)                                                                     \
-    if (mont) k_trtri_leaf<U, D, true><<<1, 512, 0, st>>>(T, ldt, n, M);                     \
-    else k_trtri_leaf<U, D, false><<<1, 512, 0, st>>>(T, ldt, n, M);
+    if (mont) launch_pdl(k_trtri_leaf<U, D, true>, 1, 512, 0, st, T, ldt, n, M);                     \
+    else launch_pdl(k_trtri_leaf<U, D, false>, 1, 512, 0, st, T, ldt, n, M);
     if (upper && unit) { TRTRI_CASE(true, true) }
     else if (upper) { TRTRI_CASE(true, false) }
     else if (unit) { TRTRI_CASE(false, true) }
@@ -702,6 +710,7 @@ cudaError_t launch_trtri_leaf(int upper, int unit, uint32_t *T, int64_t ldt, int
 __global__ void __launch_bounds__(256)
 k_trulm_leaf(uint32_t *__restrict__ A, int64_t lda, int n, ModP M)
 {
+    pdl_enter();
     __shared__ uint32_t sA[TRI_MAX][TRI_MAX + 1];
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx / n, c = idx - i * n;
@@ -730,7 +739,7 @@ cudaError_t launch_trulm_leaf(uint32_t *A, int64_t lda, int n, ModP M, cudaStrea
 {
     if (n <= 0) return cudaSuccess;
     if (n > TRI_MAX) return cudaErrorInvalidValue;
-    k_trulm_leaf<<<1, 256, 0, st>>>(A, lda, n, M);
+    launch_pdl(k_trulm_leaf, 1, 256, 0, st, A, lda, n, M);
     return cudaGetLastError();
 }
 
@@ -741,6 +750,7 @@ template <bool UNIT_L>
 __global__ void __launch_bounds__(256)
 k_trlum_leaf(uint32_t *__restrict__ A, int64_t lda, int n, ModP M)
 {
+    pdl_enter();
     __shared__ uint32_t sA[TRI_MAX][TRI_MAX + 1];
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx / n, c = idx - i * n;
@@ -772,8 +782,8 @@ cudaError_t launch_trlum_leaf(uint32_t *A, int64_t lda, int n, int unit_l, ModP 
 {
     if (n <= 0) return cudaSuccess;
     if (n > TRI_MAX) return cudaErrorInvalidValue;
-    if (unit_l) k_trlum_leaf<true><<<1, 256, 0, st>>>(A, lda, n, M);
-    else k_trlum_leaf<false><<<1, 256, 0, st>>>(A, lda, n, M);
+    if (unit_l) launch_pdl(k_trlum_leaf<true>, 1, 256, 0, st, A, lda, n, M);
+    else launch_pdl(k_trlum_leaf<false>, 1, 256, 0, st, A, lda, n, M);
     return cudaGetLastError();
 }
 
@@ -784,6 +794,7 @@ __global__ void __launch_bounds__(256)
 k_col_swaps(uint32_t *__restrict__ A, int64_t lda, int64_t nrows, const int64_t *__restrict__ list,
             int64_t count, int reverse)
 {
+    pdl_enter();
     __shared__ int64_t sl[256];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t *row = A + i * lda;
@@ -810,13 +821,14 @@ cudaError_t launch_col_swaps(uint32_t *A, int64_t lda, int64_t nrows, const int6
                              int reverse, cudaStream_t st)
 {
     if (nrows <= 0 || count <= 0) return cudaSuccess;
-    k_col_swaps<<<(unsigned)((nrows + 255) / 256), 256, 0, st>>>(A, lda, nrows, list, count, reverse);
+    launch_pdl(k_col_swaps, (unsigned)((nrows + 255) / 256), 256, 0, st, A, lda, nrows, list, count, reverse);
     return cudaGetLastError();
 }
 
 // Zero the strict upper triangle of an n x n block.
 __global__ void k_zero_upper(uint32_t *__restrict__ B, int64_t ldb, int64_t n)
 {
+    pdl_enter();
     const int64_t total = n * n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -830,6 +842,6 @@ cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t 
     if (n <= 1) return cudaSuccess;
     int64_t nb = (n * n + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_zero_upper<<<(unsigned)nb, 256, 0, st>>>(B, ldb, n);
+    launch_pdl(k_zero_upper, (unsigned)nb, 256, 0, st, B, ldb, n);
     return cudaGetLastError();
 }

@@ -123,3 +123,23 @@ def test_crt_rejects_bad_primes(lib_path):
     nw, sg = ctypes.c_int64(0), ctypes.c_int(0)
     assert lib.cup_crt(r, q, 3, w, 1, ctypes.byref(nw), ctypes.byref(sg)) == -8
     assert nw.value >= 2
+
+
+def test_every_dependent_launch_waits_for_its_predecessor():
+    """Kernels launched with programmatic dependent launch may start while the
+    previous kernel of their stream is still running; each of them must pass
+    pdl_enter() (griddepcontrol.wait) in its body. Checked on the sources."""
+    csrc = os.path.join(ROOT, "paper_1112_5717_gb300", "csrc")
+    text = "".join(open(os.path.join(csrc, f)).read() for f in sorted(os.listdir(csrc)) if f.endswith(".cu"))
+    launched = set(re.findall(r"launch_pdl\((k_\w+|tc::k_\w+|k_\w+<)", text))
+    launched = {n.replace("tc::", "").rstrip("<") for n in launched}
+    assert len(launched) >= 10
+    for name in sorted(launched):
+        m = re.search(r"__global__[^;{]*?\b" + name + r"\s*\([^{]*\{", text, flags=re.S)
+        assert m, name
+        # the kernel's body up to its matching brace
+        depth, j = 1, m.end()
+        while depth:
+            depth += {"{": 1, "}": -1}.get(text[j], 0)
+            j += 1
+        assert "pdl_enter();" in text[m.end():j], name
