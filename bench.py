@@ -495,8 +495,13 @@ def run_ours(args):
         src = "measured burst bf16 (MEASURED_PEAKS.json)"
         if peak is None:
             peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16"
+        # DRAM bytes per launch from one ncu capture of this workload's updates
+        # (profiles/k_limb_gemm_dense_full_8192_traffic.md); other workloads have none
+        traffic = (8.49e6 if (args.workload == "dense_full" and not args.n and not args.p and args.op == "factor"
+                              and engine == cup.ENGINE_TENSOR and not opts) else None)
         result["roofline"] = {"bound": "tensor", "kernel": "k_limb_gemm", "achieved": achieved, "peak": peak,
-                              "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                              "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                              "traffic_unit": "bytes per launch",
                               "peak_source": src,
                               "per_launch_ms": rst["tc_ms"] / rst["tc_launches"],
                               "launches": rst["tc_launches"],
