@@ -44,7 +44,7 @@ typedef enum {
     CUP_ERR_CUDA = -4,         /* a CUDA call failed (see cup_last_cuda_error) */
     CUP_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired */
     CUP_ERR_NOMEM = -6,        /* workspace allocation failed */
-    CUP_ERR_UNSUPPORTED = -7,  /* valid request this build cannot serve */
+    CUP_ERR_UNSUPPORTED = -7,  /* valid request the library does not serve */
     CUP_ERR_TOO_LARGE = -8     /* cup_mm_sub_noalloc: the product needs more scratch than it has */
 } cup_status;
 
