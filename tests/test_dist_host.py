@@ -1,0 +1,85 @@
+"""The benchmark's multi-rank host logic on CPU: two gloo ranks on 127.0.0.1.
+
+The factorization itself runs as independent replicas (one per GPU, no
+collective on the data path); what the ranks share is the timing protocol:
+a barrier around the timed region, the slowest rank's time and the sum of the
+ranks' operations. The reference arm runs on rank 0 only.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+_WORKER = r"""
+import os, sys, json
+sys.path.insert(0, os.environ["CUP_ROOT"])
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%s" % os.environ["MASTER_PORT"],
+                        rank=int(os.environ["RANK"]), world_size=int(os.environ["WORLD_SIZE"]))
+world, rank, local = bench.dist_env()
+bench.barrier(world)
+mx = bench.max_over_ranks(1.5 + rank, world)        # ranks hold 1.5 and 2.5
+sm = bench.sum_over_ranks(10.0 * (rank + 1), world)  # 10 + 20
+bench.barrier(world)
+print(json.dumps({"rank": rank, "world": world, "max": mx, "sum": sm}), flush=True)
+dist.destroy_process_group()
+"""
+
+
+def _run_ranks(code: str, world: int, extra_env=None, args=()):
+    port = _free_port()
+    procs = []
+    for r in range(world):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port), CUP_ROOT=ROOT, CUDA_VISIBLE_DEVICES="")
+        env.update(extra_env or {})
+        cmd = [sys.executable, "-c", code] if code else [sys.executable, os.path.join(ROOT, "bench.py"), *args]
+        procs.append(subprocess.Popen(cmd, env=env, cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                      text=True))
+    outs = []
+    for pr in procs:
+        try:
+            out, err = pr.communicate(timeout=240)
+        except subprocess.TimeoutExpired:
+            pr.kill()
+            raise
+        outs.append((pr.returncode, out, err))
+    return outs
+
+
+def test_timing_reductions_over_two_gloo_ranks():
+    outs = _run_ranks(_WORKER, 2)
+    for rc, out, err in outs:
+        assert rc == 0, err
+    got = sorted((json.loads(o.strip().splitlines()[-1]) for _, o, _ in outs), key=lambda d: d["rank"])
+    assert [d["world"] for d in got] == [2, 2]
+    assert all(d["max"] == 2.5 for d in got)
+    assert all(d["sum"] == 30.0 for d in got)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    """bench.py --impl reference under two ranks: rank 0 times the oracle on a small
+    sample and prints one JSON line; rank 1 exits 0 without output."""
+    outs = _run_ranks(None, 2, args=("--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+                                     "--cpu-sample", "96"))
+    (rc0, out0, err0), (rc1, out1, err1) = outs
+    assert rc0 == 0, err0
+    assert rc1 == 0, err1
+    assert out1.strip() == ""
+    line = json.loads(out0.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
