@@ -159,8 +159,6 @@ cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const in
                          cudaStream_t st);
 cudaError_t launch_laswp_fused(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int64_t *ipiv, Dyn k0, Dyn k1,
                                cudaStream_t st);
-cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
-                                 int64_t m, int n, ModP M, cudaStream_t st);
 cudaError_t launch_gemm_sub_cc(const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                                uint32_t *C, int64_t ldc, int64_t Mr, int64_t N, int64_t K, ModP M,
                                cudaStream_t st, int add = 0);

@@ -2,7 +2,6 @@
 //   * the row-block base case (a slab of at most CUP_BMAX rows), split into a
 //     one-CTA pivot kernel and a grid-wide finish kernel;
 //   * column transpositions (the A2 <- A2 P1^T and V1 <- V1 P2^T steps);
-//   * the TRSM(Right, Upper, Unit) leaf of the recursive triangular solve;
 //   * the CUDA-core INT64 Schur update C <- C - A B mod p (plain path, and the
 //     thin-K fallback of the tensor-core path).
 //
@@ -894,50 +893,6 @@ k_laswp_fused(uint32_t *__restrict__ A, int64_t lda, const Dyn row0d, const Dyn 
 }
 
 // ---------------------------------------------------------------------------
-// TRSM(Right, Upper, Unit) leaf: B[:, 0:n) <- B[:, 0:n) U^{-1} for an n x n
-// (n <= 64) unit upper block U (Algorithm 2 at its base, unit diagonal).
-// One warp per row: lane j holds columns j and j + 32; at step k the final
-// x_k is broadcast and every later column subtracts x_k u_kj.
-// ---------------------------------------------------------------------------
-#define TRSM_LEAF 64
-#define TRSM_WARPS 8
-template <bool MONT>
-__global__ void __launch_bounds__(32 * TRSM_WARPS)
-k_trsm_ruu_leaf(const uint32_t *__restrict__ U, int64_t ldu, uint32_t *__restrict__ B, int64_t ldb,
-                int64_t m, int n, ModP M)
-{
-    // U in Montgomery form (u R mod p) when p is odd, so that redc(x u R) = x u
-    __shared__ uint32_t sU[TRSM_LEAF][TRSM_LEAF];
-    for (int idx = threadIdx.x; idx < TRSM_LEAF * TRSM_LEAF; idx += blockDim.x) {
-        int k = idx / TRSM_LEAF, j = idx - k * TRSM_LEAF;
-        uint32_t u = (j > k && j < n && k < n) ? U[k * ldu + j] : 0u;
-        sU[k][j] = MONT ? redc((uint64_t)u * M.r2, M) : u;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * TRSM_WARPS;
-    for (int64_t i = (int64_t)blockIdx.x * TRSM_WARPS + (threadIdx.x >> 5); i < m; i += nw) {
-        uint32_t *row = B + i * ldb;
-        uint32_t x0 = (lane < n) ? row[lane] : 0u;
-        uint32_t x1 = (lane + 32 < n) ? row[lane + 32] : 0u;
-        for (int k = 0; k < n; ++k) {
-            const uint32_t xk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
-            if (xk) {
-                if (MONT) {
-                    x0 = subm(x0, redc((uint64_t)xk * sU[k][lane], M), M);
-                    x1 = subm(x1, redc((uint64_t)xk * sU[k][lane + 32], M), M);
-                } else {
-                    x0 = subm(x0, mulm(xk, sU[k][lane], M), M);
-                    x1 = subm(x1, mulm(xk, sU[k][lane + 32], M), M);
-                }
-            }
-        }
-        if (lane < n) row[lane] = x0;
-        if (lane + 32 < n) row[lane + 32] = x1;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Plain CUDA-core Schur update C <- C - A B mod p (Algorithm 1, alpha = -1,
 // beta = 1). 64 x 64 tiles, 4 x 4 outputs per thread, exact 64-bit products;
 // when K (p-1)^2 may reach 2^64 the accumulators also count wraps.
@@ -1111,18 +1066,6 @@ cudaError_t launch_laswp_fused(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, co
     if (nrows.hi <= 0 || k1.hi <= k0.lo) return cudaSuccess;
     int64_t nb = (nrows.hi + 255) / 256;
     return launch_pdl(k_laswp_fused, (unsigned)nb, 256, 0, st, A, lda, row0, nrows, ipiv, k0, k1);
-}
-
-cudaError_t launch_trsm_ruu_leaf(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb,
-                                 int64_t m, int n, ModP M, cudaStream_t st)
-{
-    if (m <= 0 || n <= 0) return cudaSuccess;
-    if (n > TRSM_LEAF) return cudaErrorInvalidValue;
-    int64_t nb = (m + TRSM_WARPS - 1) / TRSM_WARPS;
-    if (nb > 152 * 16) nb = 152 * 16;
-    if (M.p & 1u) k_trsm_ruu_leaf<true><<<(unsigned)nb, 32 * TRSM_WARPS, 0, st>>>(U, ldu, B, ldb, m, n, M);
-    else k_trsm_ruu_leaf<false><<<(unsigned)nb, 32 * TRSM_WARPS, 0, st>>>(U, ldu, B, ldb, m, n, M);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_cc_desc(const GemmDesc &d, ModP M, cudaStream_t st)
