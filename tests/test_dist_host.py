@@ -83,3 +83,24 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_operation_counts_follow_table_1():
+    """The benchmark's leading-term counts: CUP's 2mnr - (m+n)r^2 + 2/3 r^3 (the oracle's
+    exact count of the recursion, to leading order), and Table 1's constants for the square nonsingular case
+    (reduced echelon transform 2 n^3, TRLUM 2/3 n^3, InPlaceMM CUP + 2 TRMM + TRLUM)."""
+    import numpy as np
+
+    import bench
+    import oracle
+    assert bench.cup_ops(8192, 8192, 8192) == pytest.approx(2.0 / 3.0 * 8192 ** 3)
+    prof = np.arange(0, 3000, dtype=np.int64)
+    assert bench.cup_ops(16384, 4096, 3000) == pytest.approx(oracle.opcount(16384, 4096, prof), rel=1e-3)
+    n = 1024
+    assert bench.op_ops("factor", n, n, n) == pytest.approx(2.0 / 3.0 * n ** 3)
+    assert bench.op_ops("inverse", n, n, n) == pytest.approx(2.0 * n ** 3)
+    assert bench.op_ops("rref", n, n, n) == pytest.approx(2.0 * n ** 3)
+    assert bench.op_ops("trlum", n, n, n) == pytest.approx(2.0 / 3.0 * n ** 3)
+    assert bench.op_ops("inplace_mm", n, n, n) == pytest.approx((2.0 / 3.0 + 2.0 + 2.0 / 3.0) * n ** 3)
+    with pytest.raises(SystemExit):
+        bench.op_ops("inverse", n, n, n - 1)
