@@ -72,6 +72,8 @@ def parse_args(argv=None):
                          "2: every kernel class)")
     ap.add_argument("--roofline-steps", type=int, default=1,
                     help="extra untimed steps run with per-launch GEMM timing for the roofline object")
+    ap.add_argument("--no-schur", action="store_true",
+                    help="skip the isolated Schur-update measurement (16384^3 over GF(251))")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only warm-up and timed factorisations (for profiler launch lists)")
     return ap.parse_args(argv)
@@ -113,6 +115,33 @@ def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def shard_indices(count: int, world: int, rank: int) -> list:
+    """The batched workload's matrices this rank factors: every world-th one, from
+    its rank on (round robin, so every rank gets the same mix of sizes and primes)."""
+    return list(range(rank, count, world))
+
+
+def gather_batched(count: int, idx: list, recs: list, world: int) -> list:
+    """Host-side gather of the per-matrix results of every rank's shard (recs[i] is
+    the result of matrix idx[i]: its rank, determinant and row rank profile) into one
+    list indexed by matrix, on every rank. There is no device collective: the factor
+    launches never exchange data."""
+    parts = [(list(idx), list(recs))]
+    if world > 1:
+        import torch.distributed as dist
+        parts = [None] * world
+        dist.all_gather_object(parts, (list(idx), list(recs)))
+    out = [None] * count
+    for ii, rr in parts:
+        for b, rec in zip(ii, rr):
+            if out[b] is not None:
+                raise RuntimeError(f"matrix {b} factored by two ranks")
+            out[b] = rec
+    if any(r is None for r in out):
+        raise RuntimeError("a matrix of the batch was factored by no rank")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -385,12 +414,21 @@ def run_ours(args):
     engine = cup.ENGINE_TENSOR if args.engine == "tensor" else cup.ENGINE_PLAIN
     wname, mats = make_workload(args)
     batched = args.workload == "batched"
+    count_all = len(mats)
+    shard = list(range(count_all))
+    if batched and world > 1:
+        # the batch's matrices are independent problems: each rank factors its share
+        shard = shard_indices(count_all, world, rank)
+        mats = [mats[i] for i in shard]
 
     # pristine inputs resident in HBM (and pinned host copies for the end-to-end leg)
     if args.op == "int_det":
         # the integer matrix: the residues centred around zero, int64
         hosts = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.int64) - int(q) // 2).pin_memory()
                  for A, q in mats]
+    elif mats[0][0].dtype == np.uint8 and args.op in ("factor", "det", "inverse"):
+        # one-byte storage at the boundary (the library widens a working copy itself)
+        hosts = [torch.from_numpy(np.ascontiguousarray(A)).pin_memory() for A, _ in mats]
     else:
         hosts = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).pin_memory()
                  for A, _ in mats]
@@ -464,22 +502,28 @@ def run_ours(args):
         h.set_option(cup.OPT_PROFILE, 0)
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, world)
-    value = ops * world / (ms_max * 1e-3) / 1e9
+    # replicas: every rank did the same work; a sharded batch: each rank its share
+    ops_all = sum_over_ranks(ops, world) if batched else ops * world
+    value = ops_all / (ms_max * 1e-3) / 1e9
     shape = {"matrices": len(mats)} if batched else {"m": mats[0][0].shape[0], "n": mats[0][0].shape[1],
                                                      "p": primes[0], "rank": ranks_v[0]}
     result = {"metric": op_metric(args.op), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-              "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+              "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+              "scaling": "strong" if (batched and world > 1) else "weak",
+              "vs_baseline": None, "dtype": "u8" if hosts[0].dtype == torch.uint8 else "u32", "data": "synthetic",
               "config": dict({"workload": wname + (" (one persistent launch)" if batched else
                                                    (f", in-place CUP (Algorithm 6), {args.engine} Schur updates" if args.op == "factor" else
                                                     f", {args.op} through the library (CUP, Algorithms 5 and 7-9 or Sec. 5), "
                                                     f"{args.engine} Schur updates")),
-                              "engine": args.engine, "leading_term_ops": ops,
+                              "engine": args.engine, "leading_term_ops": ops_all,
                               "limbs": (cup_limbs(primes[0]) if args.op != "int_det" else 4)
                                        if engine == cup.ENGINE_TENSOR else None,
-                              "l2": "inputs restored by a device copy before each step; "
-                                    "the 256 MiB 8192^2 input exceeds the 129 MiB L2",
-                              "parallelism": "replicas" if world > 1 else "single", "options": opts,
+                              "l2": "inputs restored by a device copy before each step; the inputs total "
+                                    f"{sum(t.numel() * t.element_size() for t in hosts) / 2**20:.0f} MiB "
+                                    "(the L2 holds 129 MiB)",
+                              "parallelism": ("sharded batch: every rank factors every world-th matrix"
+                                              if batched else "replicas") if world > 1 else "single",
+                              "options": opts,
                               "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}, **shape),
               "gpu_launches": int(st["launches"]),
               "clocks": clk}
@@ -495,13 +539,11 @@ def run_ours(args):
         src = "measured burst bf16 (MEASURED_PEAKS.json)"
         if peak is None:
             peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16"
-        # DRAM bytes per launch from one ncu capture of this workload's updates
-        # (profiles/k_limb_gemm_dense_full_8192_traffic.md); other workloads have none
-        traffic = (8.49e6 if (args.workload == "dense_full" and not args.n and not args.p and args.op == "factor"
-                              and engine == cup.ENGINE_TENSOR and not opts) else None)
+        traffic, tnote = captured_traffic(wkey(args, opts, engine == cup.ENGINE_TENSOR))
         result["roofline"] = {"bound": "tensor", "kernel": "k_limb_gemm", "achieved": achieved, "peak": peak,
                               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                              "traffic_unit": "bytes per launch",
+                              "traffic_unit": "bytes per launch", "traffic_source": tnote,
+                              "algorithmic_bytes_per_launch": rst.get("tc_alg_bytes", 0.0) / rst["tc_launches"],
                               "peak_source": src,
                               "per_launch_ms": rst["tc_ms"] / rst["tc_launches"],
                               "launches": rst["tc_launches"],
@@ -512,6 +554,8 @@ def run_ours(args):
         result["roofline"] = {"bound": "alu", "kernel": "k_gemm_sub_cc",
                               "achieved": rst["cc_field_flops"] / (rst["cc_ms"] * 1e-3) / 1e12,
                               "peak": None, "unit": "Tfield-op/s", "frac": None, "traffic": None}
+    if world == 1 and not args.no_schur and not args.kernel_only:
+        result["schur"] = measure_schur(cup, dev, stream, peaks)
     result["stats"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
     if args.profile >= 2:
         result["class_ms_per_step"] = {k: round(v / args.steps, 3) for k, v in h.class_ms().items() if v}
@@ -583,6 +627,76 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# DRAM traffic per launch of the tensor-core update, from an ncu capture, keyed by
+# workload and valid only for the kernel source it was taken with.
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "roofline_traffic.json")
+TC_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1112_5717_gb300", "csrc", "cup_tc.cu")
+
+
+def wkey(args, opts, tensor: bool) -> str:
+    """Name of the timed configuration in the traffic file (default options only)."""
+    if opts or not tensor or args.p:
+        return ""
+    return f"{args.workload}:{args.n or 'default'}:{args.op}"
+
+
+def captured_traffic(key: str):
+    """(bytes per launch, source) from the traffic file when it holds a capture of this
+    configuration taken with the current tensor-kernel source; else (None, why)."""
+    import hashlib
+    try:
+        data = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None, "no ncu capture recorded"
+    rec = data.get(key) if key else None
+    if not rec:
+        return None, "no ncu capture of this configuration"
+    sha = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
+    if rec.get("source_sha256") != sha:
+        return None, "stale: the tensor kernel changed since its ncu capture"
+    return rec["bytes_per_launch"], rec.get("capture", "ncu")
+
+
+def measure_schur(cup, dev, stream, peaks, n: int = 16384, p: int = 251, warm: int = 2, steps: int = 3):
+    """The Schur update C <- C - A B mod p alone at n^3 over GF(251) (one centred
+    8-bit limb, the 32768^2 workload's update shape at n >= 16384), tensor engine:
+    CUDA events on the library's stream around the tensor-core kernel only (the
+    limb split is a separate launch, timed with the call)."""
+    import torch
+    g = torch.Generator(device=f"cuda:{dev}")
+    g.manual_seed(16384)
+    A = torch.randint(0, p, (n, n), dtype=torch.int32, device=dev, generator=g)
+    B = torch.randint(0, p, (n, n), dtype=torch.int32, device=dev, generator=g)
+    C0 = torch.randint(0, p, (n, n), dtype=torch.int32, device=dev, generator=g)
+    C = torch.empty_like(C0)
+    hs = cup.Handle(dev, engine=cup.ENGINE_TENSOR, profile=1)
+    calls = []
+    for i in range(warm + steps):
+        C.copy_(C0)
+        if i == warm:
+            hs.reset_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs.mm_sub(C, A, B, p, engine=cup.ENGINE_TENSOR)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warm:
+            calls.append(e0.elapsed_time(e1))
+    st = hs.stats()
+    hs.close()
+    L = cup_limbs(p)
+    kms = st["tc_ms"] / max(st["tc_launches"], 1)
+    limb = 2.0 * L * L * n * n * n
+    peak = peaks.get("bf16_tflops") or 1900.0
+    achieved = limb / (kms * 1e-3) / 1e12
+    return {"m": n, "n": n, "k": n, "p": p, "limbs": L,
+            "instruction": "tcgen05.mma.cta_group::1.kind::f16 (bf16 digits, fp32 accumulate in TMEM)",
+            "kernel_ms": kms, "call_ms": statistics.mean(calls), "achieved": achieved, "unit": "TFLOP/s",
+            "peak": peak, "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)" if peaks.get("bf16_tflops")
+            else "fallback 1.9 PFLOP/s bf16", "frac": achieved / peak,
+            "field_tops": 2.0 * n * n * n / (kms * 1e-3) / 1e12}
 
 
 def cup_limbs(p: int) -> int:

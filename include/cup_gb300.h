@@ -12,6 +12,7 @@
  * - Matrices are caller-owned DEVICE buffers of uint32 residues in [0, p),
  *   row-major with a leading dimension ld >= number of columns (zero-based
  *   indices and half-open ranges, Sec. 1.1). The library never frees them.
+ *   The *_u8 entry points take one-byte residues for p < 2^8 instead.
  * - Index outputs (rank profile, pivots) are caller-owned DEVICE int64 arrays.
  * - Scalars returned through plain pointers (rank, determinant) are HOST
  *   pointers; a call that returns one synchronises `stream` before returning.
@@ -86,6 +87,8 @@ typedef struct {
     int64_t cc_launches;       /* CUDA-core Schur-update kernels */
     double cc_ms;
     double cc_field_flops;
+    double tc_alg_bytes;       /* algorithmic HBM bytes of the tcgen05 launches: limb planes read
+                                  (2 L (M + N) K) plus C read and written (8 M N), summed */
 } cup_stats;
 
 /* Create a handle bound to CUDA device `device` (the device is made current
@@ -136,6 +139,36 @@ cup_status cup_factor(cup_handle *handle, uint32_t *A, int64_t m, int64_t n, int
 cup_status cup_factor_host(cup_handle *handle, const uint32_t *hA, int64_t ldh, uint32_t *hOut, uint32_t *A,
                            int64_t m, int64_t n, int64_t lda, uint32_t p, int64_t *d_profile, int64_t *d_ipiv,
                            int64_t *rank, void *stream);
+
+/* ---- One-byte residue storage (p < 2^8) ----
+ * The same operations for matrices stored as uint8 residues in [0, p), row-major
+ * with leading dimension lda (in entries, i.e. bytes), for a prime p below 2^8
+ * (CUP_ERR_ARG otherwise). The matrix keeps its one-byte storage at the
+ * boundary and in the caller's buffers: the call widens it into a uint32 working
+ * copy owned by the handle (4 m n bytes, kept for later calls), runs the uint32
+ * path on it, and narrows the result (residues below p fit a byte) back into A.
+ * Outputs, pivots, profile and rank are those of the uint32 calls on the same
+ * values. Each call synchronises `stream` before returning. */
+
+/* cup_factor on a one-byte matrix: A <- [C\U] (Algorithm 6). */
+cup_status cup_factor_u8(cup_handle *handle, uint8_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                         int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, void *stream);
+
+/* cup_factor_host on a one-byte matrix: hA (HOST, m x n, ldh bytes a row) is
+ * copied in row chunks into A (DEVICE bytes, lda), each chunk widened on the
+ * copy stream as it lands, so the copies overlap the elimination; the result is
+ * narrowed into A and copied to hOut (may equal hA). Moves m n bytes each way. */
+cup_status cup_factor_host_u8(cup_handle *handle, const uint8_t *hA, int64_t ldh, uint8_t *hOut, uint8_t *A,
+                              int64_t m, int64_t n, int64_t lda, uint32_t p, int64_t *d_profile, int64_t *d_ipiv,
+                              int64_t *rank, void *stream);
+
+/* cup_det on a one-byte square matrix (A receives the [C\U] factors). */
+cup_status cup_det_u8(cup_handle *handle, uint8_t *A, int64_t n, int64_t lda, uint32_t p, uint32_t *det,
+                      void *stream);
+
+/* cup_inverse on a one-byte square matrix: A <- A^{-1} (Algorithm 8), or
+ * CUP_SINGULAR with A holding the [C\U] factors. */
+cup_status cup_inverse_u8(cup_handle *handle, uint8_t *A, int64_t n, int64_t lda, uint32_t p, void *stream);
 
 /*
  * Rank and row rank profile (Sec. 2; Prop. 3). A is destroyed (it receives
@@ -360,20 +393,25 @@ cup_status cup_inplace_mm(cup_handle *handle, uint32_t *A, int64_t m, int64_t ld
                           int64_t ldb, uint32_t p, int64_t *rank, void *stream);
 
 /* Allocation-free Schur update: C <- C - A B mod p on the tensor engine,
- * like cup_mm_sub with CUP_ENGINE_TENSOR, for callers that must not allocate
- * device memory (for example code that runs while a stream is being captured
- * into a CUDA graph, a process whose device memory is owned by its own
- * fixed-size pool, or a latency-bound loop where an allocation is not
- * acceptable). The paper has no counterpart: this is a packaging choice.
+ * like cup_mm_sub with CUP_ENGINE_TENSOR, for callers that cannot call
+ * cudaMalloc: a process whose device memory is all reserved up front by its
+ * own fixed-size pool (a further cudaMalloc would fail, or would take memory
+ * the pool has promised elsewhere), code that has given up allocation after
+ * start-up (cudaMalloc and cudaFree may synchronise the whole device, which a
+ * latency-bound loop sharing the GPU with other streams cannot afford), or a
+ * host whose rules forbid dynamic allocation outside initialisation. The
+ * paper has no counterpart: this is a packaging choice.
  *   - No handle and no allocation: the 8-bit limb planes live in one fixed
  *     scratch array of 16 MiB that the library holds on every GPU where it
  *     is loaded, until the process exits. A product needs
  *     L * (M + N) * roundup(K, 64) * 2 bytes of it (L = 1, 2, 3, 4 limbs for
  *     p below 2^8, 2^16, 2^24, 2^31); larger products return
- *     CUP_ERR_TOO_LARGE without touching C.
- *   - Runs on the current CUDA device. The first call on a device looks up
- *     the scratch array's device address (and sets the kernel's shared-memory
- *     limit); make that first call before any stream capture.
+ *     CUP_ERR_TOO_LARGE without touching C. The call allocates nothing itself
+ *     and calls no allocating library routine.
+ *   - Runs on the current CUDA device. The first call on each device does the
+ *     set-up, with that device current: it looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) and raises the kernel's shared-memory
+ *     limit on that device. Make that first call before any stream capture.
  *   - Every call on a device shares the one scratch array and its error word:
  *     calls that can overlap on the GPU (different streams, or several host
  *     threads) race and must be serialised by the caller. Each call rewrites
@@ -383,6 +421,16 @@ cup_status cup_inplace_mm(cup_handle *handle, uint32_t *A, int64_t m, int64_t ld
 cup_status cup_mm_sub_noalloc(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
                               const uint32_t *B, int64_t ldb, int64_t M, int64_t N, int64_t K,
                               uint32_t p, void *stream);
+
+/* Self-test of failure detection (no counterpart in the paper): one device
+ * thread waits, with the same bounded wait the tensor-core kernels use, on an
+ * mbarrier that nothing arrives at. After limit_us microseconds (1 .. 10^7)
+ * the wait gives up, records its site in the handle's device error word and
+ * the kernel returns; the call then reads the word like every other call and
+ * returns CUP_ERR_TIMEOUT with "device wait expired (site 99)" in
+ * cup_last_cuda_error. The word is cleared again, so the handle and the CUDA
+ * context stay usable. Synchronises `stream`. */
+cup_status cup_selftest_wait(cup_handle *handle, int64_t limit_us, void *stream);
 
 /* Column transpositions (Sec. 1.1): for t = k0..k1-1 in order, swap columns t
  * and d_ipiv[t] of rows row0..row0+nrows-1 of A (A <- A P^T restricted to

@@ -31,7 +31,7 @@ class Stats(ctypes.Structure):
                 ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
                 ("tc_limb_flops", ctypes.c_double), ("tc_field_flops", ctypes.c_double),
                 ("cc_launches", ctypes.c_int64), ("cc_ms", ctypes.c_double),
-                ("cc_field_flops", ctypes.c_double)]
+                ("cc_field_flops", ctypes.c_double), ("tc_alg_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +82,11 @@ SIGNATURES = {
     "cup_primes_below": (_INT, [_U32, _I64, _U32P, _I64P]),
     "cup_mm_sub_noalloc": (_INT, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _P]),
     "cup_factor_batched": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "cup_selftest_wait": (_INT, [_P, _I64, _P]),
+    "cup_factor_u8": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
+    "cup_factor_host_u8": (_INT, [_P, _P, _I64, _P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
+    "cup_det_u8": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
+    "cup_inverse_u8": (_INT, [_P, _P, _I64, _I64, _U32, _P]),
 }
 
 
@@ -131,12 +136,13 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _mat(t, what):
+def _mat(t, what, u8_ok: bool = False):
     torch = _torch()
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{what} must be a CUDA tensor")
-    if t.dtype not in (torch.int32,):
-        raise TypeError(f"{what} must be torch.int32 holding residues in [0, p)")
+    if t.dtype not in ((torch.int32, torch.uint8) if u8_ok else (torch.int32,)):
+        raise TypeError(f"{what} must be torch.int32 holding residues in [0, p)"
+                        + (" (or torch.uint8 for p < 2^8)" if u8_ok else ""))
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError(f"{what} must be a row-major 2-D tensor (unit column stride)")
     return t.shape[0], t.shape[1], max(t.stride(0), 1)
@@ -188,7 +194,7 @@ class Handle:
     def _check(self, st, what, h):
         if st not in (0,):
             detail = ""
-            if h is not None and st == -4:
+            if h is not None and st in (-4, -5):
                 detail = self.lib.cup_last_cuda_error(h).decode()
             raise CupError(st, what, detail)
 
@@ -221,19 +227,28 @@ class Handle:
         except Exception:
             pass
 
+    def selftest_wait(self, limit_us: int = 200000, stream=None):
+        """Run cup_selftest_wait: a device wait that nothing completes, given up after
+        limit_us. Returns (status, message); status is -5 (CUP_ERR_TIMEOUT) when the
+        bounded wait and its reporting work."""
+        st = self.lib.cup_selftest_wait(self.h, int(limit_us), _stream_ptr(stream))
+        return st, self.lib.cup_last_cuda_error(self.h).decode()
+
     # --- entry points -----------------------------------------------------
     def factor(self, A, p: int, stream=None):
         """In-place CUP (Algorithm 6): A <- [C\\U]; returns (rank, profile, ipiv)
-        with profile/ipiv int64 device tensors of length min(m, n) (first rank valid)."""
+        with profile/ipiv int64 device tensors of length min(m, n) (first rank valid).
+        A torch.uint8 matrix (p < 2^8) goes through cup_factor_u8."""
         torch = _torch()
-        m, n, lda = _mat(A, "A")
+        m, n, lda = _mat(A, "A", u8_ok=True)
         k = max(min(m, n), 1)
         prof = torch.empty(k, dtype=torch.int64, device=A.device)
         ipiv = torch.empty(k, dtype=torch.int64, device=A.device)
         r = ctypes.c_int64(0)
-        st = self.lib.cup_factor(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(),
-                                 ipiv.data_ptr(), ctypes.byref(r), _stream_ptr(stream))
-        self._check(st, "cup_factor", self.h)
+        fn = "cup_factor_u8" if A.dtype == torch.uint8 else "cup_factor"
+        st = getattr(self.lib, fn)(self.h, A.data_ptr(), m, n, lda, p, prof.data_ptr(),
+                                   ipiv.data_ptr(), ctypes.byref(r), _stream_ptr(stream))
+        self._check(st, fn, self.h)
         return r.value, prof, ipiv
 
     def factor_host(self, hA, A, p: int, out=None, stream=None):
@@ -241,24 +256,26 @@ class Handle:
         device work tensor A in row chunks that overlap the factorization, and [C\\U]
         comes back into `out` (default: hA itself). Returns (rank, profile, ipiv)."""
         torch = _torch()
-        if not isinstance(hA, torch.Tensor) or hA.is_cuda or hA.dtype != torch.int32 or hA.dim() != 2 \
+        dt = A.dtype if isinstance(A, torch.Tensor) else None
+        if not isinstance(hA, torch.Tensor) or hA.is_cuda or hA.dtype != dt or hA.dim() != 2 \
                 or hA.stride(1) != 1:
-            raise TypeError("hA must be a row-major CPU torch.int32 tensor")
+            raise TypeError("hA must be a row-major CPU tensor of A's dtype")
         out = hA if out is None else out
-        if not isinstance(out, torch.Tensor) or out.is_cuda or out.dtype != torch.int32 or out.shape != hA.shape \
+        if not isinstance(out, torch.Tensor) or out.is_cuda or out.dtype != dt or out.shape != hA.shape \
                 or out.stride() != hA.stride():
-            raise TypeError("out must be a CPU torch.int32 tensor laid out like hA")
-        m, n, lda = _mat(A, "A")
+            raise TypeError("out must be a CPU tensor laid out like hA")
+        m, n, lda = _mat(A, "A", u8_ok=True)
         if tuple(hA.shape) != (m, n):
             raise ValueError("hA and A must have the same shape")
         k = max(min(m, n), 1)
         prof = torch.empty(k, dtype=torch.int64, device=A.device)
         ipiv = torch.empty(k, dtype=torch.int64, device=A.device)
         r = ctypes.c_int64(0)
-        st = self.lib.cup_factor_host(self.h, hA.data_ptr(), max(hA.stride(0), 1), out.data_ptr(), A.data_ptr(),
-                                      m, n, lda, p, prof.data_ptr(), ipiv.data_ptr(), ctypes.byref(r),
-                                      _stream_ptr(stream))
-        self._check(st, "cup_factor_host", self.h)
+        fn = "cup_factor_host_u8" if dt == torch.uint8 else "cup_factor_host"
+        st = getattr(self.lib, fn)(self.h, hA.data_ptr(), max(hA.stride(0), 1), out.data_ptr(), A.data_ptr(),
+                                   m, n, lda, p, prof.data_ptr(), ipiv.data_ptr(), ctypes.byref(r),
+                                   _stream_ptr(stream))
+        self._check(st, fn, self.h)
         return r.value, prof, ipiv
 
     def rank_profile(self, A, p: int, stream=None):
@@ -272,23 +289,27 @@ class Handle:
         return r.value, prof[: r.value]
 
     def det(self, A, p: int, stream=None) -> int:
-        n, n2, lda = _mat(A, "A")
+        torch = _torch()
+        n, n2, lda = _mat(A, "A", u8_ok=True)
         if n != n2:
             raise ValueError("det needs a square matrix")
         d = ctypes.c_uint32(0)
-        st = self.lib.cup_det(self.h, A.data_ptr(), n, lda, p, ctypes.byref(d), _stream_ptr(stream))
-        self._check(st, "cup_det", self.h)
+        fn = "cup_det_u8" if A.dtype == torch.uint8 else "cup_det"
+        st = getattr(self.lib, fn)(self.h, A.data_ptr(), n, lda, p, ctypes.byref(d), _stream_ptr(stream))
+        self._check(st, fn, self.h)
         return int(d.value)
 
     def inverse(self, A, p: int, stream=None) -> bool:
         """A <- A^{-1} in place; returns False (A holds [C\\U]) if A is singular."""
-        n, n2, lda = _mat(A, "A")
+        torch = _torch()
+        n, n2, lda = _mat(A, "A", u8_ok=True)
         if n != n2:
             raise ValueError("inverse needs a square matrix")
-        st = self.lib.cup_inverse(self.h, A.data_ptr(), n, lda, p, _stream_ptr(stream))
+        fn = "cup_inverse_u8" if A.dtype == torch.uint8 else "cup_inverse"
+        st = getattr(self.lib, fn)(self.h, A.data_ptr(), n, lda, p, _stream_ptr(stream))
         if st == 1:
             return False
-        self._check(st, "cup_inverse", self.h)
+        self._check(st, fn, self.h)
         return True
 
     def rref(self, A, p: int, want_x: bool = False, stream=None):

@@ -52,6 +52,8 @@ struct cup_handle {
     int64_t rank_at_cap = 0;
     uint32_t *d_backup = nullptr;  // input copy for the exact fallback
     size_t backup_bytes = 0;
+    uint32_t *d_wide = nullptr;    // uint32 working copy of a one-byte-storage matrix
+    size_t wide_bytes = 0;
     int64_t *h_rank = nullptr;     // pinned copy of rank_at after a device-resident run
     int64_t h_rank_cap = 0;
     struct Timed;
@@ -62,8 +64,11 @@ struct cup_handle {
         bool no_capture;                  // capture failed once: stay eager
         std::vector<int> timed;           // indices into graph_timed, read after each replay
         std::vector<GemmDesc> gemms;      // the Schur updates it runs (extents resolved per replay)
-        const uint32_t *hA = nullptr;     // host input copied in by the graph (cup_factor_host)
+        const void *hA = nullptr;         // host input copied in by the graph (cup_factor_host)
         int64_t ldh = 0;
+        const uint8_t *dev8 = nullptr;    // one-byte input (or its staging copy) widened by the graph
+        int64_t ld8 = 0;
+        int esize = 4;
     };
     int64_t gen = 0;                   // bumped whenever a buffer a graph may reference moves
     std::vector<GraphEntry> graphs;
@@ -278,6 +283,7 @@ cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, in
         h->stats.tc_launches += 1;
         h->stats.tc_field_flops += f;
         h->stats.tc_limb_flops += f * L * L;
+        h->stats.tc_alg_bytes += 2.0 * L * (double)(M + N) * (double)K + 8.0 * (double)M * (double)N;
         if (h->profile) h->pending.push_back({e0, e1, f * L * L, f, 0});
         return CUP_OK;
     }
@@ -491,7 +497,8 @@ cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_ou
         CU(cudaMemcpyAsync(h->h_pinned, h->d_slab, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
         {
         ClassTimer tm(h, c.st, 3);
-        CU(launch_slab_finish(c.A, c.lda, a, dconst(col0), c.n, c.M, h->d_slab, nullptr, c.st));
+        CU(launch_slab_finish(c.A, c.lda, a, dconst(col0), c.n, c.M, h->d_slab, nullptr, c.st,
+                              h->engine == CUP_ENGINE_TENSOR));
         }
         h->stats.launches += 2;
         CK(sync_stream(h, c.st));
@@ -649,7 +656,8 @@ cup_status dev_rec(DevCtx &c, int64_t a, int64_t mrows)
         }
         {
             ClassTimer tm(h, c.st, 3);
-            CU(launch_slab_finish(c.A, c.lda, a, col0, c.n, c.M, h->d_slab, h->d_err, c.st));
+            CU(launch_slab_finish(c.A, c.lda, a, col0, c.n, c.M, h->d_slab, h->d_err, c.st,
+                                  h->engine == CUP_ENGINE_TENSOR));
         }
         h->stats.launches += 2;
         return CUP_OK;
@@ -715,13 +723,49 @@ cudaError_t launch_cup_batched(const cup_batch_item *items, int64_t count, int64
 
 namespace {
 
-// hA (host, leading dimension ldh), if given, is the input: it is copied into A in
-// row chunks on a second stream, and the factorization waits for a chunk only
-// when it first touches one of its rows (the recursion reaches the rows in order).
+// Where the input of a factorization comes from. By default it is already in A
+// (uint32, on the device). With `host` it is a host matrix of esize-byte entries
+// (4: uint32, 1: uint8) copied in by the call; a one-byte host input lands in the
+// device bytes dev8 first. With dev8 and no host it is a device matrix of bytes.
+// One-byte inputs are widened into A, the call's uint32 working copy.
+struct InputSrc {
+    const void *host = nullptr;
+    int64_t ldh = 0;
+    int esize = 4;
+    uint8_t *dev8 = nullptr;
+    int64_t ld8 = 0;
+};
+
+// Rows [r0, r1) of the input into A, on stream `st`.
+cup_status load_rows(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, int64_t r0, int64_t r1, const InputSrc &src,
+                     cudaStream_t st)
+{
+    if (r1 <= r0) return CUP_OK;
+    if (src.host && src.esize == 4) {
+        CU(cudaMemcpy2DAsync(A + r0 * lda, (size_t)lda * 4, (const uint32_t *)src.host + r0 * src.ldh,
+                             (size_t)src.ldh * 4, (size_t)n * 4, (size_t)(r1 - r0), cudaMemcpyHostToDevice, st));
+        return CUP_OK;
+    }
+    if (src.host)
+        CU(cudaMemcpy2DAsync(src.dev8 + r0 * src.ld8, (size_t)src.ld8, (const uint8_t *)src.host + r0 * src.ldh,
+                             (size_t)src.ldh, (size_t)n, (size_t)(r1 - r0), cudaMemcpyHostToDevice, st));
+    if (src.dev8) {
+        CU(launch_widen_u8(A + r0 * lda, lda, src.dev8 + r0 * src.ld8, src.ld8, r1 - r0, n, st));
+        h->stats.launches += 1;
+    }
+    return CUP_OK;
+}
+
+// A host input is copied into A in row chunks on a second stream, and the
+// factorization waits for a chunk only when it first touches one of its rows (the
+// recursion reaches the rows in order); a device byte input is widened into A by
+// the first launch.
 cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
                          int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, cudaStream_t st,
-                         const uint32_t *hA = nullptr, int64_t ldh = 0)
+                         const InputSrc &src)
 {
+    const void *hA = src.host;
+    const int64_t ldh = src.ldh;
     const int64_t nleaves = count_leaves(m, h->leaf_rows);
     if (nleaves + 1 > h->rank_at_cap) {
         if (h->d_rank_at) cudaFree(h->d_rank_at);
@@ -731,8 +775,11 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
         h->rank_at_cap = nleaves + 1;
         ++h->gen;
     }
+    // the exact fallback restarts from a copy of a device input (a host input is
+    // simply copied in again), so only device inputs need the m n backup
     const size_t bbytes = (size_t)m * (size_t)n * 4;
-    if (bbytes > h->backup_bytes) {
+    const bool backup = !hA && !src.dev8;
+    if (backup && bbytes > h->backup_bytes) {
         if (h->d_backup) cudaFree(h->d_backup);
         h->d_backup = nullptr;
         h->backup_bytes = 0;
@@ -760,7 +807,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
     cup_handle::GraphEntry *ge = nullptr;
     for (auto &e : h->graphs)
         if (e.A == A && e.m == m && e.n == n && e.lda == lda && e.p == p && e.prof == d_profile && e.hA == hA &&
-            e.ldh == ldh &&
+            e.ldh == ldh && e.dev8 == src.dev8 && e.ld8 == src.ld8 && e.esize == src.esize &&
             e.ipiv == d_ipiv && e.st == st && e.leaf_rows == h->leaf_rows && e.window == h->window &&
             e.engine == h->engine && e.tc_min_k == h->tc_min_k)
             ge = &e;
@@ -790,13 +837,14 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
             CU(cudaStreamWaitEvent(h->copy, h->ev_fork, 0));
             for (size_t i = 0; i < chunk_row.size(); ++i) {
                 const int64_t r0 = chunk_row[i], r1 = i + 1 < chunk_row.size() ? chunk_row[i + 1] : m;
-                CU(cudaMemcpy2DAsync(A + r0 * lda, (size_t)lda * 4, hA + r0 * ldh, (size_t)ldh * 4, (size_t)n * 4,
-                                     (size_t)(r1 - r0), cudaMemcpyHostToDevice, h->copy));
+                CK(load_rows(h, A, lda, n, r0, r1, src, h->copy));
                 CU(cudaEventRecord(h->chunk_ev[i], h->copy));
             }
             c.chunk_row = chunk_row.data();
             c.chunk_ev = h->chunk_ev.data();
             c.nchunk = (int)chunk_row.size();
+        } else if (src.dev8) {
+            CK(load_rows(h, A, lda, n, 0, m, src, st));
         } else {
             CU(cudaMemcpy2DAsync(h->d_backup, (size_t)n * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m,
                                  cudaMemcpyDeviceToDevice, st));
@@ -845,7 +893,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
             h->pending.resize(pend0);
             h->stats.launches = launches0;
             ge->gemms.clear();
-            return factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, hA, ldh);
+            return factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, src);
         }
         ge->exec = exec;
         ge->launches = h->stats.launches - launches0;
@@ -863,7 +911,8 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
         if (!ge && h->use_graph && capturable) {
             // remember the call; the next identical one is captured and replayed
             cup_handle::GraphEntry e{A, m, n, lda, p, d_profile, d_ipiv, st, h->leaf_rows, h->window, h->engine,
-                                     h->tc_min_k, h->gen, nullptr, 0, false, {}, {}, hA, ldh};
+                                     h->tc_min_k, h->gen, nullptr, 0, false, {}, {}, hA, ldh, src.dev8, src.ld8,
+                                     src.esize};
             if (h->graphs.size() > 16) {
                 if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
                 h->graphs.erase(h->graphs.begin());
@@ -892,12 +941,14 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
         // the extents each Schur update actually had, from the ranks this run produced
         const int L = tc_limbs(p);
         for (const auto &g : *glist) {
-            const double f = 2.0 * (double)g.M * (double)host_eval(g.N, h->d_rank_at, h->h_rank) *
-                             (double)host_eval(g.K, h->d_rank_at, h->h_rank);
+            const double gn = (double)host_eval(g.N, h->d_rank_at, h->h_rank),
+                         gk = (double)host_eval(g.K, h->d_rank_at, h->h_rank);
+            const double f = 2.0 * (double)g.M * gn * gk;
             if (g.add) {
                 h->stats.tc_launches += 1;
                 h->stats.tc_field_flops += f;
                 h->stats.tc_limb_flops += f * L * L;
+                h->stats.tc_alg_bytes += 2.0 * L * ((double)g.M + gn) * gk + 8.0 * (double)g.M * gn;
             } else {
                 h->stats.cc_launches += 1;
                 h->stats.cc_field_flops += f;
@@ -915,6 +966,96 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
     }
     *rank = r;
     return CUP_OK;
+}
+
+cup_status ensure_wide(cup_handle *h, size_t bytes)
+{
+    if (bytes <= h->wide_bytes) return CUP_OK;
+    if (h->d_wide) cudaFree(h->d_wide);
+    h->d_wide = nullptr;
+    h->wide_bytes = 0;
+    CU(cudaMalloc(&h->d_wide, bytes));
+    h->wide_bytes = bytes;
+    ++h->gen;
+    return CUP_OK;
+}
+
+// CUP of the input described by src into A (m x n, lda): the device-resident
+// schedule (schedule 1), or the host-driven one (schedule 0, and the exact
+// fallback when a row taken as dependent was not), which first loads the input
+// again: from the host, from the device bytes, or from the backup copy that the
+// device-resident run made of a uint32 device input.
+cup_status factor_impl(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                       int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, cudaStream_t st, const InputSrc &src)
+{
+    cup_status s = CUP_ERR_SPECULATION_INTERNAL;
+    if (h->schedule == 1) s = factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, src);
+    if (s != CUP_ERR_SPECULATION_INTERNAL) return s;
+    if (src.host || src.dev8) {
+        CK(load_rows(h, A, lda, n, 0, m, src, st));
+    } else if (h->schedule == 1) {
+        CU(cudaMemcpy2DAsync(A, (size_t)lda * 4, h->d_backup, (size_t)n * 4, (size_t)n * 4, (size_t)m,
+                             cudaMemcpyDeviceToDevice, st));
+    }
+    if (h->schedule == 1) ++h->stats.host_syncs;
+    Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, st};
+    int64_t r = 0;
+    CK(cup_rec(c, 0, m, 0, &r));
+    CK(check_device_error(h, st));
+    *rank = r;
+    return CUP_OK;
+}
+
+// Determinant from the factorization of the input described by src into A (n x n).
+cup_status det_impl(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t p, uint32_t *det, cudaStream_t st,
+                    const InputSrc &src)
+{
+    int64_t *d_idx = nullptr;
+    uint32_t *d_out = nullptr;
+    CU(cudaMalloc(&d_idx, 2 * (size_t)n * sizeof(int64_t)));
+    int64_t r = 0;
+    cup_status s = factor_impl(h, A, n, n, lda, p, d_idx, d_idx + n, &r, st, src);
+    if (s == CUP_OK) {
+        if (r < n) {
+            *det = 0;
+        } else {
+            s = cuda_ok(h, cudaMalloc(&d_out, sizeof(uint32_t)));
+            if (s == CUP_OK) s = cuda_ok(h, launch_det_reduce(A, lda, n, d_idx + n, make_modp(p), d_out, st));
+            if (s == CUP_OK)
+                s = cuda_ok(h, cudaMemcpyAsync(h->h_pinned, d_out, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            if (s == CUP_OK) s = sync_stream(h, st);
+            h->stats.launches += 1;
+            if (s == CUP_OK) *det = (uint32_t)h->h_pinned[0];
+        }
+    }
+    cudaFree(d_idx);
+    if (d_out) cudaFree(d_out);
+    return s;
+}
+
+// In-place inverse (Algorithm 8 via Algorithm 7) of the input described by src, in A.
+cup_status inverse_impl(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t p, cudaStream_t st,
+                        const InputSrc &src)
+{
+    int64_t *d_idx = nullptr;
+    CU(cudaMalloc(&d_idx, 2 * (size_t)n * sizeof(int64_t)));
+    int64_t r = 0;
+    const ModP M = make_modp(p);
+    cup_status s = factor_impl(h, A, n, n, lda, p, d_idx, d_idx + n, &r, st, src);
+    if (s == CUP_OK && r < n) s = CUP_SINGULAR;
+    if (s == CUP_OK) s = red_col_ech(h, A, n, n, lda, r, d_idx, M, h->engine, st);
+    // A^{-1} = P^T X1: row swaps (j, ipiv[j]) for j = n-1 down to 0
+    if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(A, lda, n, d_idx + n, n, 0, 0, 1, 0, st));
+    if (s == CUP_OK) s = check_device_error(h, st);
+    cudaFree(d_idx);
+    return s;
+}
+
+// Checks shared by the one-byte entry points: p below 2^8 and prime.
+cup_status check_u8(uint32_t p)
+{
+    if (p >= 256u) return CUP_ERR_ARG;
+    return check_prime(p);
 }
 
 }  // namespace
@@ -954,6 +1095,7 @@ cup_status cup_destroy(cup_handle *h)
         for (cudaEvent_t e : h->chunk_ev) cudaEventDestroy(e);
         if (h->d_rank_at) cudaFree(h->d_rank_at);
         if (h->d_backup) cudaFree(h->d_backup);
+        if (h->d_wide) cudaFree(h->d_wide);
         if (h->h_rank) cudaFreeHost(h->h_rank);
         for (auto &g2 : h->graphs)
             if (g2.exec) cudaGraphExecDestroy(g2.exec);
@@ -1043,20 +1185,7 @@ cup_status cup_factor(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t 
     if (n >= (int64_t)1 << 31) return CUP_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     CK(ensure_base(h));
-    Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, (cudaStream_t)stream};
-    if (h->schedule == 1) {
-        cup_status s = factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, c.st);
-        if (s != CUP_ERR_SPECULATION_INTERNAL) return s;
-        // a row taken as dependent was not: redo exactly from the saved input
-        CU(cudaMemcpy2DAsync(A, (size_t)lda * 4, h->d_backup, (size_t)n * 4, (size_t)n * 4, (size_t)m,
-                             cudaMemcpyDeviceToDevice, c.st));
-        ++h->stats.host_syncs;
-    }
-    int64_t r = 0;
-    CK(cup_rec(c, 0, m, 0, &r));
-    CK(check_device_error(h, c.st));
-    *rank = r;
-    return CUP_OK;
+    return factor_impl(h, A, m, n, lda, p, d_profile, d_ipiv, rank, (cudaStream_t)stream, InputSrc{});
 }
 
 cup_status cup_factor_host(cup_handle *h, const uint32_t *hA, int64_t ldh, uint32_t *hOut, uint32_t *A, int64_t m,
@@ -1072,21 +1201,62 @@ cup_status cup_factor_host(cup_handle *h, const uint32_t *hA, int64_t ldh, uint3
     DeviceGuard g(h->device);
     CK(ensure_base(h));
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t wb = (size_t)n * 4;
-    cup_status s = CUP_ERR_SPECULATION_INTERNAL;
-    if (h->schedule == 1) s = factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, hA, ldh);
-    if (s == CUP_ERR_SPECULATION_INTERNAL) {
-        // host-driven schedule, or a row taken as dependent was not: redo exactly from the host input
-        CU(cudaMemcpy2DAsync(A, (size_t)lda * 4, hA, (size_t)ldh * 4, wb, (size_t)m, cudaMemcpyHostToDevice, st));
-        Ctx c{h, A, lda, n, make_modp(p), d_ipiv, d_profile, st};
-        int64_t r = 0;
-        CK(cup_rec(c, 0, m, 0, &r));
-        CK(check_device_error(h, st));
-        *rank = r;
-        s = CUP_OK;
-    }
-    CK(s);
-    CU(cudaMemcpy2DAsync(hOut, (size_t)ldh * 4, A, (size_t)lda * 4, wb, (size_t)m, cudaMemcpyDeviceToHost, st));
+    InputSrc src;
+    src.host = hA;
+    src.ldh = ldh;
+    CK(factor_impl(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, src));
+    CU(cudaMemcpy2DAsync(hOut, (size_t)ldh * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m, cudaMemcpyDeviceToHost,
+                         st));
+    return sync_stream(h, st);
+}
+
+cup_status cup_factor_u8(cup_handle *h, uint8_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                         int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_u8(p));
+    *rank = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!A || !d_profile || !d_ipiv) return CUP_ERR_ARG;
+    if (n >= (int64_t)1 << 31) return CUP_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(ensure_wide(h, (size_t)m * (size_t)n * 4));
+    cudaStream_t st = (cudaStream_t)stream;
+    InputSrc src;
+    src.esize = 1;
+    src.dev8 = A;
+    src.ld8 = lda;
+    CK(factor_impl(h, h->d_wide, m, n, n, p, d_profile, d_ipiv, rank, st, src));
+    CU(launch_narrow_u8(A, lda, h->d_wide, n, m, n, st));
+    h->stats.launches += 1;
+    return sync_stream(h, st);
+}
+
+cup_status cup_factor_host_u8(cup_handle *h, const uint8_t *hA, int64_t ldh, uint8_t *hOut, uint8_t *A, int64_t m,
+                              int64_t n, int64_t lda, uint32_t p, int64_t *d_profile, int64_t *d_ipiv, int64_t *rank,
+                              void *stream)
+{
+    if (!h || !rank || m < 0 || n < 0 || lda < (n > 0 ? n : 1) || ldh < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_u8(p));
+    *rank = 0;
+    if (m == 0 || n == 0) return CUP_OK;
+    if (!hA || !hOut || !A || !d_profile || !d_ipiv) return CUP_ERR_ARG;
+    if (n >= (int64_t)1 << 31) return CUP_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(ensure_wide(h, (size_t)m * (size_t)n * 4));
+    cudaStream_t st = (cudaStream_t)stream;
+    InputSrc src;
+    src.host = hA;
+    src.ldh = ldh;
+    src.esize = 1;
+    src.dev8 = A;
+    src.ld8 = lda;
+    CK(factor_impl(h, h->d_wide, m, n, n, p, d_profile, d_ipiv, rank, st, src));
+    CU(launch_narrow_u8(A, lda, h->d_wide, n, m, n, st));
+    h->stats.launches += 1;
+    CU(cudaMemcpy2DAsync(hOut, (size_t)ldh, A, (size_t)lda, (size_t)n, (size_t)m, cudaMemcpyDeviceToHost, st));
     return sync_stream(h, st);
 }
 
@@ -1160,31 +1330,28 @@ cup_status cup_det(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t 
     if (n == 0) { *det = 1u % p; return CUP_OK; }
     if (!A) return CUP_ERR_ARG;
     DeviceGuard g(h->device);
-    int64_t *d_idx = nullptr;
-    uint32_t *d_out = nullptr;
-    CU(cudaMalloc(&d_idx, 2 * (size_t)n * sizeof(int64_t)));
-    cup_status s = CUP_OK;
-    int64_t r = 0;
-    s = cup_factor(h, A, n, n, lda, p, d_idx, d_idx + n, &r, stream);
-    if (s == CUP_OK) {
-        if (r < n) {
-            *det = 0;
-        } else {
-            s = cuda_ok(h, cudaMalloc(&d_out, sizeof(uint32_t)));
-            if (s == CUP_OK)
-                s = cuda_ok(h, launch_det_reduce(A, lda, n, d_idx + n, make_modp(p), d_out,
-                                                 (cudaStream_t)stream));
-            if (s == CUP_OK)
-                s = cuda_ok(h, cudaMemcpyAsync(h->h_pinned, d_out, sizeof(uint32_t),
-                                               cudaMemcpyDeviceToHost, (cudaStream_t)stream));
-            if (s == CUP_OK) s = sync_stream(h, (cudaStream_t)stream);
-            h->stats.launches += 1;
-            if (s == CUP_OK) *det = (uint32_t)h->h_pinned[0];
-        }
-    }
-    cudaFree(d_idx);
-    if (d_out) cudaFree(d_out);
-    return s;
+    CK(ensure_base(h));
+    return det_impl(h, A, n, lda, p, det, (cudaStream_t)stream, InputSrc{});
+}
+
+cup_status cup_det_u8(cup_handle *h, uint8_t *A, int64_t n, int64_t lda, uint32_t p, uint32_t *det, void *stream)
+{
+    if (!h || !det || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_u8(p));
+    if (n == 0) { *det = 1u % p; return CUP_OK; }
+    if (!A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(ensure_wide(h, (size_t)n * (size_t)n * 4));
+    cudaStream_t st = (cudaStream_t)stream;
+    InputSrc src;
+    src.esize = 1;
+    src.dev8 = A;
+    src.ld8 = lda;
+    CK(det_impl(h, h->d_wide, n, n, p, det, st, src));
+    CU(launch_narrow_u8(A, lda, h->d_wide, n, n, n, st));
+    h->stats.launches += 1;
+    return sync_stream(h, st);
 }
 
 cup_status cup_inverse(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint32_t p, void *stream)
@@ -1194,18 +1361,30 @@ cup_status cup_inverse(cup_handle *h, uint32_t *A, int64_t n, int64_t lda, uint3
     if (n == 0) return CUP_OK;
     if (!A) return CUP_ERR_ARG;
     DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    return inverse_impl(h, A, n, lda, p, (cudaStream_t)stream, InputSrc{});
+}
+
+cup_status cup_inverse_u8(cup_handle *h, uint8_t *A, int64_t n, int64_t lda, uint32_t p, void *stream)
+{
+    if (!h || n < 0 || lda < (n > 0 ? n : 1)) return CUP_ERR_ARG;
+    CK(check_u8(p));
+    if (n == 0) return CUP_OK;
+    if (!A) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    CK(ensure_wide(h, (size_t)n * (size_t)n * 4));
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t *d_idx = nullptr;
-    CU(cudaMalloc(&d_idx, 2 * (size_t)n * sizeof(int64_t)));
-    int64_t r = 0;
-    const ModP M = make_modp(p);
-    cup_status s = cup_factor(h, A, n, n, lda, p, d_idx, d_idx + n, &r, stream);
-    if (s == CUP_OK && r < n) s = CUP_SINGULAR;
-    if (s == CUP_OK) s = red_col_ech(h, A, n, n, lda, r, d_idx, M, h->engine, st);
-    // A^{-1} = P^T X1: row swaps (j, ipiv[j]) for j = n-1 down to 0
-    if (s == CUP_OK) s = cuda_ok(h, launch_row_swaps(A, lda, n, d_idx + n, n, 0, 0, 1, 0, st));
-    if (s == CUP_OK) s = check_device_error(h, st);
-    cudaFree(d_idx);
+    InputSrc src;
+    src.esize = 1;
+    src.dev8 = A;
+    src.ld8 = lda;
+    const cup_status s = inverse_impl(h, h->d_wide, n, n, p, st, src);
+    if (s != CUP_OK && s != CUP_SINGULAR) return s;
+    // the inverse, or the [C\U] factors of a singular input
+    CU(launch_narrow_u8(A, lda, h->d_wide, n, n, n, st));
+    h->stats.launches += 1;
+    CK(sync_stream(h, st));
     return s;
 }
 
@@ -1495,6 +1674,18 @@ cup_status cup_trlum(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, uint32_
     CK(trlum(h, A, lda, n, 1, make_modp(p), h->engine, (cudaStream_t)stream));
     CK(check_device_error(h, (cudaStream_t)stream));
     return CUP_OK;
+}
+
+cup_status cup_selftest_wait(cup_handle *h, int64_t limit_us, void *stream)
+{
+    if (!h || limit_us < 1 || limit_us > 10000000) return CUP_ERR_ARG;
+    DeviceGuard g(h->device);
+    CK(ensure_base(h));
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    CU(launch_selftest_wait(h->d_err, (uint64_t)limit_us * 1000ull, CUP_DEVERR_SELFTEST, st));
+    h->stats.launches += 1;
+    return check_device_error(h, st);
 }
 
 cup_status cup_factor_batched(cup_handle *h, const cup_batch_item *d_items, int64_t count, int64_t *d_rank,

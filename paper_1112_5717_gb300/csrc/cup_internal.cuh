@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA translation units of the CUP library.
 #pragma once
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 #include "modp.cuh"
 
@@ -75,6 +77,32 @@ static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 blo
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
+// One-time setup per CUDA device (kernel attributes such as the raised dynamic
+// shared-memory limit belong to each device's context): `setup` runs, with the
+// device current, the first time a launcher is used on that device, and again
+// after a failure. Thread safe; the common path is one atomic load.
+struct PerDeviceOnce {
+    static constexpr int kMaxDev = 128;
+    std::atomic<uint64_t> done[kMaxDev / 64] = {};
+    std::mutex mu;
+};
+template <typename F>
+static inline cudaError_t once_per_device(PerDeviceOnce &o, F setup)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= PerDeviceOnce::kMaxDev) return setup();
+    const uint64_t bit = 1ull << (dev & 63);
+    std::atomic<uint64_t> &w = o.done[dev >> 6];
+    if (w.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(o.mu);
+    if (w.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+    e = setup();
+    if (e == cudaSuccess) w.fetch_or(bit, std::memory_order_release);
+    return e;
 }
 
 static inline Dyn dconst(int64_t v) { return Dyn{v, nullptr, nullptr, 0, 0, v, v}; }
@@ -152,8 +180,10 @@ struct SlabScratch {
 cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int brows, Dyn col0, int64_t n,
                                int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv, int64_t *prof,
                                int64_t *rank_next, cudaStream_t st);
+// tensor: U = L^{-1} X by bf16 digit products on mma.sync for p < 2^24 (the tensor
+// engine); otherwise, and for the plain engine, by 64-bit CUDA-core products.
 cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, int64_t n, ModP M,
-                               const SlabScratch *S, int *err, cudaStream_t st);
+                               const SlabScratch *S, int *err, cudaStream_t st, bool tensor);
 cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st);
 cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int2 *pairs, const int *count,
                          cudaStream_t st);
@@ -175,6 +205,11 @@ cudaError_t launch_gemm_sub_tc(const uint32_t *A, int64_t lda, const uint32_t *B
                                int64_t ldc, int64_t M, int64_t N, int64_t K, ModP Mp, void *ws, int *err,
                                cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
                                int add = 0);
+
+// Bounded-wait self-test (cup_tc.cu): a wait that nothing completes, given up
+// after limit_ns with `code` recorded in *err.
+#define CUP_DEVERR_SELFTEST 99
+cudaError_t launch_selftest_wait(int *err, uint64_t limit_ns, int code, cudaStream_t st);
 
 // Triangular building blocks (cup_tri.cu). Flags of launch_tri_leaf: the
 // triangle T is n x n with n = rows (left) or cols (right) of B, n <= 64.
@@ -200,6 +235,11 @@ cudaError_t launch_transpose(uint32_t *D, int64_t ldd, const uint32_t *S, int64_
 cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds, int64_t m, int64_t n,
                         cudaStream_t st);
 cudaError_t launch_zero_upper(uint32_t *B, int64_t ldb, int64_t n, cudaStream_t st);
+// One-byte residue storage: W (uint32, ldw) <- B8 (uint8, ld8) and back, m x n.
+cudaError_t launch_widen_u8(uint32_t *W, int64_t ldw, const uint8_t *B8, int64_t ld8, int64_t m, int64_t n,
+                            cudaStream_t st);
+cudaError_t launch_narrow_u8(uint8_t *B8, int64_t ld8, const uint32_t *W, int64_t ldw, int64_t m, int64_t n,
+                             cudaStream_t st);
 
 // Prime check shared by the entry points (cup_api.cu).
 bool cup_internal_prime_ok(uint32_t p);

@@ -979,19 +979,21 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
                                int wn, int speculate, ModP M, SlabScratch *S, int64_t *ipiv, int64_t *prof,
                                int64_t *rank_next, cudaStream_t st)
 {
-    static bool attr = false;
+    static PerDeviceOnce attr;
     // window rows, then the row-operation matrix
     const size_t smem = ((size_t)CUP_BMAX * PIV_LDW + (size_t)CUP_BMAX * PIV_LDE) * sizeof(uint32_t);
     (void)brows;
-    if (!attr) {
-        const int mx = (int)smem;
-        cudaError_t e = cudaFuncSetAttribute(k_slab_pivots<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_slab_pivots<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_slab_pivots<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    {
+        const cudaError_t e = once_per_device(attr, [&] {
+            const int mx = (int)smem;
+            cudaError_t e2 = cudaFuncSetAttribute(k_slab_pivots<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(k_slab_pivots<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(k_slab_pivots<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            return e2;
+        });
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     // the block update sums PIV_PB + 1 products below p^2 in 64 bits when that cannot wrap
     const uint64_t pm1 = M.p - 1u;
@@ -1011,27 +1013,27 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
 }
 
 cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, int64_t n, ModP M,
-                               const SlabScratch *S, int *err, cudaStream_t st)
+                               const SlabScratch *S, int *err, cudaStream_t st, bool tensor)
 {
     const int64_t wmax = n - col0.lo;
     int64_t nb = (wmax + CUP_QT - 1) / CUP_QT;
     if (nb <= 0) return cudaSuccess;
     const uint32_t p = M.p;
-    if (p < (1u << 24)) {
+    if (tensor && p < (1u << 24)) {
         // tensor-core product of l-limb digits; the recombined value is below 2^55 in size
         const int l = p < (1u << 8) ? 1 : p < (1u << 16) ? 2 : 3;
         const uint64_t off = ((1ull << 55) / p + 1) * p;
         const int smem = 2 * l * CUP_BMAX * FIN_LD * 2;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_slab_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 1 * CUP_BMAX * FIN_LD * 2);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_slab_finish<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 2 * CUP_BMAX * FIN_LD * 2);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_slab_finish<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 3 * CUP_BMAX * FIN_LD * 2);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        static PerDeviceOnce attr;
+        const cudaError_t e = once_per_device(attr, [] {
+            cudaError_t e2 = cudaFuncSetAttribute(k_slab_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 1 * CUP_BMAX * FIN_LD * 2);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(k_slab_finish<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 2 * CUP_BMAX * FIN_LD * 2);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(k_slab_finish<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 3 * CUP_BMAX * FIN_LD * 2);
+            return e2;
+        });
+        if (e != cudaSuccess) return e;
         SlabScratch *Sm = const_cast<SlabScratch *>(S);
         if (l == 1) return launch_pdl(k_slab_finish<2>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
         if (l == 2) return launch_pdl(k_slab_finish<3>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
@@ -1040,9 +1042,9 @@ cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, in
     }
     // a row of Linv times a column of X sums CUP_BMAX products: wide sums unless CUP_BMAX (p-1)^2 < 2^64
     const bool wide = (long double)CUP_BMAX * (M.p - 1) * (long double)(M.p - 1) >= 18446744073709551615.0L;
-    if (wide) k_slab_finish<1><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err, 0);
-    else k_slab_finish<0><<<(unsigned)nb, 256, 0, st>>>(A, lda, a, col0, n, M, const_cast<SlabScratch *>(S), err, 0);
-    return cudaGetLastError();
+    SlabScratch *Sm = const_cast<SlabScratch *>(S);
+    if (wide) return launch_pdl(k_slab_finish<1>, (unsigned)nb, 256, 0, st, A, lda, a, col0, n, M, Sm, err, (uint64_t)0);
+    return launch_pdl(k_slab_finish<0>, (unsigned)nb, 256, 0, st, A, lda, a, col0, n, M, Sm, err, (uint64_t)0);
 }
 
 cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st)

@@ -71,8 +71,10 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
-// Bounded wait: gives up after ~2 s of wall time and records the failure.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
+// Bounded wait: gives up after limit_ns of wall time (2 s in the kernels), or as
+// soon as another thread has recorded a failure, and records the failure.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
+                                          uint64_t limit_ns = 2000000000ull)
 {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -80,12 +82,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
         if (mbar_try(bar, parity)) return true;
         if ((it & 255u) == 0u) {
             if (*(volatile int *)err != 0) return false;
-            if (globaltimer() - t0 > 2000000000ull) {
+            if (globaltimer() - t0 > limit_ns) {
                 atomicCAS(err, 0, code);
                 return false;
             }
         }
     }
+}
+
+// Self-test of the timeout path: one thread waits, with the kernels' bounded
+// wait, on an mbarrier that nothing arrives at; the wait gives up after
+// limit_ns, records `code` in the error word and the kernel returns normally.
+__global__ void k_selftest_wait(int *err, uint64_t limit_ns, int code)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(smem_u32(&bar), 0u, err, code, limit_ns);
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
@@ -600,11 +614,12 @@ cudaError_t run_cfg(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t
     CUtensorMap ta, tb;
     if (!make_map(&ta, Al, Kp, M, L, BM) || !make_map(&tb, Bl, Kp, Nmax, L, CF::BN))
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_limb_gemm<L, BNX>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
+    static PerDeviceOnce attr;
+    {
+        const cudaError_t e = once_per_device(attr, [] {
+            return cudaFuncSetAttribute(k_limb_gemm<L, BNX>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
+        });
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     // offset making the recombined chunk value nonnegative: a multiple of p above its bound
     const int bound_bits = (L <= 3) ? 60 : 52;
@@ -626,6 +641,12 @@ cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
 }
 
 }  // namespace tc
+
+cudaError_t launch_selftest_wait(int *err, uint64_t limit_ns, int code, cudaStream_t st)
+{
+    tc::k_selftest_wait<<<1, 32, 0, st>>>(err, limit_ns, code);
+    return cudaGetLastError();
+}
 
 int tc_limbs(uint32_t p)
 {

@@ -432,16 +432,18 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
 {
     if (d.rows <= 0 || d.n.hi <= 0) return cudaSuccess;
     if (d.n.hi > RUU_MAX) return cudaErrorInvalidValue;
-    static bool attr = false;
+    static PerDeviceOnce attr;
     const size_t smem = ((size_t)RUU_MAX * RUU_LDS + 4 * 32 * TRI_VLD) * sizeof(uint32_t);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsm_ruu128<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm_ruu128<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm_ruu128<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = once_per_device(attr, [&] {
+            cudaError_t e2 = cudaFuncSetAttribute(k_trsm_ruu128<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(k_trsm_ruu128<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(k_trsm_ruu128<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return e2;
+        });
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     // one wave of CTAs (two fit an SM): every CTA loads the triangle and, for p < 2^16,
     // inverts its diagonal blocks, so more rows per CTA spread that fixed cost
@@ -626,6 +628,69 @@ cudaError_t launch_copy(uint32_t *D, int64_t ldd, const uint32_t *S, int64_t lds
     if (nb > 152 * 32) nb = 152 * 32;
     launch_pdl(k_copy, (unsigned)nb, 256, 0, st, D, ldd, S, lds, m, n);
     return cudaGetLastError();
+}
+
+// One-byte residue storage (p < 2^8) at the ABI: the factorization works on a
+// uint32 copy. k_widen copies an m x n block of bytes into 32-bit words, k_narrow
+// copies words (residues below 256) back to bytes. A thread moves 16 entries of a
+// row: one 16-byte load and four 16-byte stores (or the reverse) when the row
+// offsets are aligned, single entries otherwise. Both are HBM-bound copies.
+template <bool NARROW>
+__global__ void __launch_bounds__(256)
+k_widen_narrow(uint8_t *__restrict__ B8, int64_t ld8, uint32_t *__restrict__ W, int64_t ldw, int64_t m, int64_t n)
+{
+    pdl_enter();
+    const int64_t per_row = (n + 15) / 16, total = m * per_row;
+    const bool vec = ((ld8 | ldw) & 15) == 0 && (((uintptr_t)B8 | (uintptr_t)W) & 15) == 0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / per_row, j0 = (idx - i * per_row) * 16;
+        uint8_t *b = B8 + i * ld8 + j0;
+        uint32_t *w = W + i * ldw + j0;
+        if (vec && j0 + 16 <= n) {
+            if (NARROW) {
+                uint32_t v[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) *(uint4 *)&v[4 * q] = ((const uint4 *)w)[q];
+                uint4 o;
+                o.x = v[0] | v[1] << 8 | v[2] << 16 | v[3] << 24;
+                o.y = v[4] | v[5] << 8 | v[6] << 16 | v[7] << 24;
+                o.z = v[8] | v[9] << 8 | v[10] << 16 | v[11] << 24;
+                o.w = v[12] | v[13] << 8 | v[14] << 16 | v[15] << 24;
+                *(uint4 *)b = o;
+            } else {
+                const uint4 x = *(const uint4 *)b;
+                const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    ((uint4 *)w)[q] = make_uint4(wd[q] & 255u, (wd[q] >> 8) & 255u, (wd[q] >> 16) & 255u, wd[q] >> 24);
+            }
+        } else {
+            const int cnt = (int)(n - j0 < 16 ? n - j0 : 16);
+            for (int c = 0; c < cnt; ++c) {
+                if (NARROW) b[c] = (uint8_t)w[c];
+                else w[c] = b[c];
+            }
+        }
+    }
+}
+
+cudaError_t launch_widen_u8(uint32_t *W, int64_t ldw, const uint8_t *B8, int64_t ld8, int64_t m, int64_t n,
+                            cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m * ((n + 15) / 16) + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    return launch_pdl(k_widen_narrow<false>, (unsigned)nb, 256, 0, st, const_cast<uint8_t *>(B8), ld8, W, ldw, m, n);
+}
+
+cudaError_t launch_narrow_u8(uint8_t *B8, int64_t ld8, const uint32_t *W, int64_t ldw, int64_t m, int64_t n,
+                             cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int64_t nb = (m * ((n + 15) / 16) + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    return launch_pdl(k_widen_narrow<true>, (unsigned)nb, 256, 0, st, B8, ld8, const_cast<uint32_t *>(W), ldw, m, n);
 }
 
 // ---------------------------------------------------------------------------

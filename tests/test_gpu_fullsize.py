@@ -1,24 +1,35 @@
-"""Parity at the benchmark's full sizes, in the launch configuration bench.py times
-(tensor engine, default options, repeated calls on a stream of our own, so the
-second call is a CUDA-graph replay; the host-buffer entry point as in the
-end-to-end leg).
+"""Parity at the benchmark workloads' full sizes, element by element against the oracle.
 
-The oracle cannot factor these sizes in test time, so the result is checked by
-properties that hold at any size and pin it down:
+The oracle's results at these sizes are stored as SHA-256 digests in
+tests/golden/fullsize_digests.json, written by tests/golden/make_fullsize_digests.py,
+which calls only the oracle and the input generators (the oracle needs minutes per
+case on the host). Each test computes the same digest of the CUDA path's output:
+equal digests mean equal arrays. The input's digest is checked first, so that a
+difference in input generation is reported as such. The CUDA calls run in the launch
+configuration bench.py times (tensor engine, default options, repeated calls on a
+stream of our own, so the second call is a CUDA-graph replay; the host-buffer entry
+point of the end-to-end leg).
+
+Before the digests, a cheap check that holds at any size runs too (and is the only
+element-wise check for the 32768^2 workload, whose oracle would need hours):
   * [C\\U] has the shape the decomposition promises (Proposition 1): C in
     column echelon form with nonzero pivots at the reported row rank profile,
     zeros outside C and U, the transpositions in LAPACK form (ipiv[t] >= t);
   * A P^T = C U, by Freivalds' test with random vectors modulo p (a wrong entry
     anywhere survives one vector with probability at most 1/p), evaluated
     exactly in 64-bit integer blocks.
-Together these make the rank and the row rank profile exact (the row rank profile
-of A P^T = C U is that of C, whose pivot rows are the reported profile).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_1112_5717_gb300 import inputs
+from tests.golden.make_fullsize_digests import digest
+
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_digests.json")
 
 pytestmark = pytest.mark.gpu
 
@@ -78,40 +89,60 @@ def check_cup_at_scale(A, packed, prof, ipiv, r, p, trials=None, seed=12):
         assert np.array_equal(y1, y2)
 
 
+def _golden(case):
+    data = json.load(open(_GOLDEN))
+    if case not in data:
+        pytest.fail(f"{case}: no oracle digest in {_GOLDEN} (run tests/golden/make_fullsize_digests.py)")
+    return data[case]
+
+
+def _check_input(rec, *arrays):
+    assert digest(*arrays) == rec["input"], "the input generator made a different matrix than the oracle's run"
+
+
+def _check_cup(rec, r, prof, ipiv, packed):
+    want = rec["cup"]
+    assert r == want["rank"]
+    assert digest(np.asarray(prof[:r], dtype=np.int64)) == want["profile"], "row rank profile differs from the oracle"
+    assert digest(np.asarray(ipiv[:r], dtype=np.int64)) == want["ipiv"], "transpositions differ from the oracle"
+    assert digest(packed) == want["packed"], "[C\\U] differs from the oracle"
+
+
 def _factor_like_bench(cup, A, p):
     """Two calls as bench.py makes them (tensor engine, default options, a stream of
     our own: the second is a graph replay); returns the host result of the second."""
     import torch
+    u8 = A.dtype == np.uint8
     h = cup.Handle(engine=cup.ENGINE_TENSOR)
-    src = torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).cuda()
+    src = torch.from_numpy(A.copy() if u8 else np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).cuda()
     work = torch.empty_like(src)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     outs = []
+
+    def host(t):
+        return t.cpu().numpy().copy() if u8 else t.cpu().numpy().view(np.uint32).copy()
+
     with torch.cuda.stream(stream):
         for _ in range(2):
             work.copy_(src)
             r, prof, ipiv = h.factor(work, p)
             torch.cuda.synchronize()
-            outs.append((r, prof[:r].cpu().numpy(), ipiv[:r].cpu().numpy(),
-                         work.cpu().numpy().view(np.uint32).copy()))
+            outs.append((r, prof[:r].cpu().numpy(), ipiv[:r].cpu().numpy(), host(work)))
     # the host-buffer entry point of the end-to-end leg, also replayed on its second call
-    hA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).pin_memory()
+    hA = src.cpu().pin_memory()
     hout = torch.empty_like(hA).pin_memory()
     with torch.cuda.stream(stream):
         for _ in range(2):
             rh, _, _ = h.factor_host(hA, work, p, out=hout)
     torch.cuda.synchronize()
     h.close()
-    return outs, rh, hout.numpy().view(np.uint32)
+    return outs, rh, (hout.numpy().copy() if u8 else hout.numpy().view(np.uint32))
 
 
-@pytest.mark.parametrize("workload", ["dense_full_8192", "rank_deficient_16384x4096"])
-def test_full_size_factorization(cuda_lib, workload):
-    if workload == "dense_full_8192":
-        A, p = inputs.dense_full(n=8192, p=inputs.P_16), inputs.P_16
-    else:
-        A, p = inputs.rank_deficient(p=inputs.P_23), inputs.P_23
+def _run_factor(cuda_lib, case, A, p):
+    rec = _golden(case)
+    _check_input(rec, A)
     outs, rh, hout = _factor_like_bench(cuda_lib, A, p)
     (r0, prof0, ipiv0, P0), (r1, prof1, ipiv1, P1) = outs
     # the replayed call reproduces the first one exactly, and so does the host-buffer call
@@ -119,5 +150,112 @@ def test_full_size_factorization(cuda_lib, workload):
     assert np.array_equal(prof0, prof1) and np.array_equal(ipiv0, ipiv1) and np.array_equal(P0, P1)
     assert np.array_equal(hout, P1)
     check_cup_at_scale(A, P1, prof1, ipiv1, r1, p)
-    if workload == "rank_deficient_16384x4096":
-        assert r1 <= 3000
+    _check_cup(rec, r1, prof1, ipiv1, P1)
+    return rec
+
+
+def test_full_size_dense_8192(cuda_lib):
+    _run_factor(cuda_lib, "dense_full_8192", inputs.dense_full(n=8192, p=inputs.P_16), inputs.P_16)
+
+
+def test_full_size_rank_deficient(cuda_lib):
+    rec = _run_factor(cuda_lib, "rank_deficient", inputs.rank_deficient(p=inputs.P_23), inputs.P_23)
+    assert rec["cup"]["rank"] <= 3000
+
+
+def test_full_size_small_p_8192_u8(cuda_lib):
+    """The 32768^2 GF(251) workload's structure (one centred 8-bit limb, one-byte
+    storage) at 8192^2, where the oracle finishes."""
+    _run_factor(cuda_lib, "dense_small_p_8192", inputs.dense_small_p(n=8192, p=inputs.P_8), inputs.P_8)
+
+
+def _freivalds_inverse(A, Ainv, p, trials):
+    """A (A^{-1} x) = x for random x modulo p."""
+    rng = np.random.default_rng(7)
+    for _ in range(trials):
+        x = rng.integers(0, p, size=A.shape[1], dtype=np.int64)
+        y = _matvec_mod(A, _matvec_mod(Ainv, x, p), p)
+        assert np.array_equal(y, x), "A A^-1 != I"
+
+
+@pytest.mark.parametrize("case", ["dense_full_8192", "dense_small_p_8192"])
+def test_full_size_det_and_inverse(cuda_lib, case):
+    import torch
+    if case == "dense_full_8192":
+        A, p = inputs.dense_full(n=8192, p=inputs.P_16), inputs.P_16
+        dev = torch.from_numpy(A.view(np.int32).copy()).cuda()
+        host = lambda t: t.cpu().numpy().view(np.uint32)          # noqa: E731
+    else:
+        A, p = inputs.dense_small_p(n=8192, p=inputs.P_8), inputs.P_8
+        dev = torch.from_numpy(A.copy()).cuda()
+        host = lambda t: t.cpu().numpy()                           # noqa: E731
+    rec = _golden(case)
+    _check_input(rec, A)
+    h = cuda_lib.Handle(engine=cuda_lib.ENGINE_TENSOR)
+    work = dev.clone()
+    assert h.det(work, p) == rec["det"], "determinant differs from the oracle"
+    work.copy_(dev)
+    assert h.inverse(work, p) == (rec["inverse"] is not None)
+    inv = host(work)
+    _freivalds_inverse(A, inv, p, trials=max(2, -(-30 // max(1, int(np.log2(p))))))
+    assert digest(inv) == rec["inverse"], "inverse differs from the oracle"
+    h.close()
+
+
+def test_full_size_rref(cuda_lib):
+    """Reduced column echelon form R and its transform X of the 16384 x 4096 workload."""
+    import torch
+    A, p = inputs.rank_deficient(p=inputs.P_23), inputs.P_23
+    rec = _golden("rank_deficient")
+    _check_input(rec, A)
+    h = cuda_lib.Handle(engine=cuda_lib.ENGINE_TENSOR)
+    dA = torch.from_numpy(A.view(np.int32).copy()).cuda()
+    r, prof, X = h.rref(dA, p, want_x=True)
+    want = rec["rref"]
+    assert r == want["rank"]
+    assert digest(prof[:r].cpu().numpy().astype(np.int64)) == want["profile"]
+    assert digest(dA.cpu().numpy().view(np.uint32)) == want["R"], "R differs from the oracle"
+    assert digest(X.cpu().numpy().view(np.uint32)) == want["X"], "X differs from the oracle"
+    h.close()
+
+
+def test_full_size_batched(cuda_lib):
+    """All 4096 matrices of the batched workload, each modulo its own prime near 2^30,
+    in the one launch bench.py times: rank, [C\\U], profile, transpositions and, for the
+    square ones, the determinant of every matrix."""
+    import torch
+    mats = inputs.batched()
+    rec = _golden("batched")
+    _check_input(rec, *[A for A, _ in mats])
+    h = cuda_lib.Handle()
+    dm = [torch.from_numpy(np.ascontiguousarray(A, dtype=np.uint32).view(np.int32)).cuda() for A, _ in mats]
+    ranks, profs, ipivs, dets = h.factor_batched(dm, [q for _, q in mats], want_det=True)
+    torch.cuda.synchronize()
+    ranks = ranks.cpu().numpy().tolist()
+    dets = dets.cpu().numpy().view(np.uint32)
+    assert ranks == rec["ranks"], [b for b, (x, y) in enumerate(zip(ranks, rec["ranks"])) if x != y][:10]
+    bad = []
+    for b, (A, q) in enumerate(mats):
+        r = ranks[b]
+        dg = digest(dm[b].cpu().numpy().view(np.uint32), profs[b][:r].cpu().numpy().astype(np.int64),
+                    ipivs[b][:r].cpu().numpy().astype(np.int64))[:16]
+        if dg != rec["cup"][b]:
+            bad.append(b)
+        if rec["det"][b] is not None and int(dets[b]) != rec["det"][b]:
+            bad.append(b)
+    assert not bad, f"matrices differing from the oracle: {sorted(set(bad))[:20]}"
+    h.close()
+
+
+def test_full_size_small_p_32768_u8(cuda_lib):
+    """The 32768^2 GF(251) workload itself (one-byte storage, as bench.py times it):
+    shape of [C\\U] and Freivalds' test of A P^T = C U, the replayed and host-buffer
+    calls equal to the first; the oracle would need hours here, so its element-wise
+    comparison is the 8192^2 case above."""
+    A, p = inputs.dense_small_p(n=32768, p=inputs.P_8), inputs.P_8
+    outs, rh, hout = _factor_like_bench(cuda_lib, A, p)
+    (r0, prof0, ipiv0, P0), (r1, prof1, ipiv1, P1) = outs
+    assert r0 == r1 == rh
+    assert np.array_equal(prof0, prof1) and np.array_equal(ipiv0, ipiv1) and np.array_equal(P0, P1)
+    assert np.array_equal(hout, P1)
+    check_cup_at_scale(A, P1, prof1, ipiv1, r1, p, trials=5)

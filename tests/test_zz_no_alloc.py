@@ -1,17 +1,21 @@
-"""The allocation-free Schur update against the handle-based one.
+"""The allocation-free Schur update against the handle-based one and the oracle.
 
-cup_mm_sub_noalloc serves callers that may not allocate device memory (for
-instance while capturing a stream into a CUDA graph, or when all device memory
-belongs to the caller's own pool): its limb scratch is a fixed array inside
-the library. This test calls it twice in a row through the C ABI and requires
-both results to equal, bit for bit, those of cup_mm_sub on the tensor engine
-for the same inputs; it also checks that a product too large for the scratch
-is refused without touching C. The file is named to run after the other tests.
+cup_mm_sub_noalloc serves callers that cannot call cudaMalloc: a process whose
+device memory is all reserved by its own fixed-size pool, or code that must not
+allocate after start-up because cudaMalloc and cudaFree may synchronise the whole
+device. Its limb scratch is a fixed array inside the library. This test calls it
+twice in a row through the C ABI and requires both results to equal, bit for bit,
+those of cup_mm_sub on the tensor engine for the same inputs and the oracle's
+C - A B mod p (Algorithm 1 with alpha = -1, beta = 1); it also checks that a product
+too large for the scratch is refused without touching C. The file is named so that
+pytest collects it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +50,9 @@ def test_noalloc_equals_handle_path_twice(cuda_lib, p):
         got = _dev(C)
         assert _call_noalloc(lib, got, _dev(A), _dev(B), p) == 0, f"call {call}"
         torch.cuda.synchronize()
-        assert torch.equal(got, want), f"call {call} differs"
+        assert torch.equal(got, want), f"call {call} differs from cup_mm_sub"
+        ref = oracle.mm_sub(C, A, B, p)
+        assert np.array_equal(got.cpu().numpy().view(np.uint32), ref), f"call {call} differs from the oracle"
     h.close()
 
 
