@@ -268,9 +268,13 @@ typedef struct {
 /*
  * Batched CUP (Algorithm 6's output for each matrix, as cup_factor) of
  * `count` independent matrices, each over its own prime field, in one
- * persistent launch; nothing is read back to the host, so the call is
- * asynchronous and can be captured in a CUDA graph. Matrices with
- * min(m, n) <= 2048 are supported.
+ * persistent launch (one CTA per SM, each factoring one matrix at a time,
+ * the largest first); nothing is read back to the host, so the call is
+ * asynchronous. A repeated call with the same arguments on a stream other
+ * than the legacy default stream replays one CUDA graph (the items are read
+ * when it runs, so their contents may change between calls). Matrices with
+ * min(m, n) <= 2048 are supported; those with at most 1024 columns are
+ * factored in 32-row panels held in shared memory.
  *   d_items  device array of `count` items.
  *   d_rank   device int64[count]: the rank of each matrix, or -1 if its item
  *            was invalid (bad sizes or pointers, p not a prime below 2^31,

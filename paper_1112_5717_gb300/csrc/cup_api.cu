@@ -39,6 +39,13 @@ struct cup_handle {
     int *h_pinned = nullptr;
     int *d_err = nullptr;          // device-side error word of the tensor-core kernels
     unsigned long long *d_next = nullptr;   // work counter of the batched kernel
+    int *d_order = nullptr;                 // its work order (largest matrices first)
+    int64_t order_cap = 0;
+    struct BatchGraph {
+        const cup_batch_item *items; int64_t count; int64_t *rank; uint32_t *det; cudaStream_t st;
+        int64_t gen; cudaGraphExec_t exec; bool no_capture;
+    };
+    std::vector<BatchGraph> bgraphs;         // batched calls replayed as graphs
     void *d_ws = nullptr;          // limb planes of the tensor-core Schur update
     size_t ws_bytes = 0;
     int profile = 0;
@@ -717,7 +724,7 @@ struct DeviceGuard {
 bool cup_internal_prime_ok(uint32_t p) { return check_prime(p) == CUP_OK; }
 
 cudaError_t launch_cup_batched(const cup_batch_item *items, int64_t count, int64_t *ranks, uint32_t *dets,
-                               unsigned long long *next, int grid, cudaStream_t st);
+                               unsigned long long *next, int *order, int grid, cudaStream_t st);
 
 #define CUP_ERR_SPECULATION_INTERNAL ((cup_status)-100)
 
@@ -1089,6 +1096,9 @@ cup_status cup_destroy(cup_handle *h)
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
         if (h->d_err) cudaFree(h->d_err);
         if (h->d_next) cudaFree(h->d_next);
+        if (h->d_order) cudaFree(h->d_order);
+        for (auto &b : h->bgraphs)
+            if (b.exec) cudaGraphExecDestroy(b.exec);
         if (h->d_ws) cudaFree(h->d_ws);
         if (h->copy) cudaStreamDestroy(h->copy);
         if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -1695,12 +1705,61 @@ cup_status cup_factor_batched(cup_handle *h, const cup_batch_item *d_items, int6
     if (count == 0) return CUP_OK;
     if (!d_items || !d_rank) return CUP_ERR_ARG;
     DeviceGuard g(h->device);
+    if (count > INT32_MAX) return CUP_ERR_UNSUPPORTED;
     if (!h->d_next) CU(cudaMalloc(&h->d_next, sizeof(unsigned long long)));
+    if (count > h->order_cap) {
+        if (h->d_order) cudaFree(h->d_order);
+        h->d_order = nullptr;
+        h->order_cap = 0;
+        CU(cudaMalloc(&h->d_order, (size_t)count * sizeof(int)));
+        h->order_cap = count;
+        ++h->gen;
+    }
     int nsm = 0;
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int64_t grid = count < (int64_t)nsm * 2 ? count : (int64_t)nsm * 2;
-    CU(launch_cup_batched(d_items, count, d_rank, d_det, h->d_next, (int)grid, (cudaStream_t)stream));
-    h->stats.launches += 1;
+    // one CTA per SM (each holds a 32-row panel of up to 1024 columns in shared memory)
+    const int64_t grid = count < (int64_t)nsm ? count : (int64_t)nsm;
+    cudaStream_t st = (cudaStream_t)stream;
+    // a repeated call with the same arguments on a stream of its own replays one graph
+    // (work counter reset, work order, factor kernel)
+    const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    cup_handle::BatchGraph *bg = nullptr;
+    for (auto &e : h->bgraphs)
+        if (e.items == d_items && e.count == count && e.rank == d_rank && e.det == d_det && e.st == st) bg = &e;
+    if (bg && bg->gen != h->gen) {
+        if (bg->exec) cudaGraphExecDestroy(bg->exec);
+        bg->exec = nullptr;
+        bg->gen = h->gen;
+    }
+    if (bg && capturable && !bg->exec && !bg->no_capture) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t e1 = launch_cup_batched(d_items, count, d_rank, d_det, h->d_next, h->d_order, (int)grid, st);
+            const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+            if (e1 == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+                exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        if (!exec) {
+            cudaGetLastError();
+            bg->no_capture = true;
+        }
+        bg->exec = exec;
+    }
+    if (bg && bg->exec && capturable) {
+        CU(cudaGraphLaunch(bg->exec, st));
+    } else {
+        if (!bg && capturable) {
+            if (h->bgraphs.size() > 16) {
+                if (h->bgraphs.front().exec) cudaGraphExecDestroy(h->bgraphs.front().exec);
+                h->bgraphs.erase(h->bgraphs.begin());
+            }
+            h->bgraphs.push_back(cup_handle::BatchGraph{d_items, count, d_rank, d_det, st, h->gen, nullptr, false});
+        }
+        CU(launch_cup_batched(d_items, count, d_rank, d_det, h->d_next, h->d_order, (int)grid, st));
+    }
+    h->stats.launches += 2;
     return CUP_OK;
 }
 

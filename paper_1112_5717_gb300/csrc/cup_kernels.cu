@@ -117,8 +117,10 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_muinv[CUP_BMAX], s_Sinv[CUP_BMAX],
         s_Sfwd[CUP_BMAX];
     __shared__ __align__(16) uint32_t s_coef[CUP_BMAX][PIV_PB];   // -a_kt of the block update, per row below a panel
-    __shared__ int s_c, s_ext;
+    __shared__ int s_c, s_ext, s_fast;
     __shared__ int s_state[2][6];              // after each panel: rank, stop, spec count, done, rows to update, swaps
+    __shared__ uint32_t s_T[PIV_PB][PIV_PB];   // fast panel path: the panel's row operations (fraction-free)
+    __shared__ uint32_t s_sprod;
     __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
 
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -167,11 +169,99 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     const int ext0 = s_ext;
 
     int r = 0, stop = brows, nspec = 0, pc = 0;
-    bool done = false;
-    uint32_t Sprod = one;                      // product of the row scales applied so far (warp 0)
+    bool done = false, try_fast = true;
+    uint32_t Sprod = one;                      // product of the row scales applied so far (every thread)
     for (; p0 < brows && !done; p0 += PIV_PB, ++pc) {
         const int pend = p0 + PIV_PB < brows ? p0 + PIV_PB : brows;
-        const int r0 = r;
+        const int r0 = r, np = pend - p0;
+        int lim = brows;
+        bool pswap = false;
+        // Fast path of a panel: when the residual of every panel row at the current rank
+        // position is nonzero, the rule takes that position as the pivot of each row in
+        // turn (no transposition, no dependent row), so the panel's steps only combine
+        // its rows. Warp 0 then eliminates the np x np diagonal block in registers (the
+        // same fraction-free steps) and records the row operations as T (panel rows after
+        // = T x panel rows before); one parallel pass applies T to the panel's other
+        // columns, instead of np steps separated by barriers. A zero on the diagonal sends
+        // this panel, and the rest of the slab, to the stepwise elimination below.
+        bool fast = false;
+        if (try_fast && r0 + np <= wne) {
+            if (warp == 0) {
+                const int k = lane >> 2, jg = lane & 3, ja = 2 * jg, jb = ja + 1;
+                const bool rk = k < np;
+                uint32_t b0 = (rk && ja < np) ? W[(p0 + k) * PIV_LDW + r0 + ja] : 0u;
+                uint32_t b1 = (rk && jb < np) ? W[(p0 + k) * PIV_LDW + r0 + jb] : 0u;
+                uint32_t t0 = (k == ja) ? one : 0u, t1 = (k == jb) ? one : 0u;
+                uint32_t fv = 0u;                     // lane t keeps the pivot of step t
+                bool ok = true;
+                for (int t = 0; t < np; ++t) {
+                    const int sf = 4 * t + (t >> 1), sm = 4 * k + (t >> 1), sy = 4 * t + jg;
+                    const uint32_t fa = __shfl_sync(0xffffffffu, b0, sf), fb = __shfl_sync(0xffffffffu, b1, sf);
+                    const uint32_t f = (t & 1) ? fb : fa;
+                    if (f == 0u) { ok = false; break; }      // the same value in every lane
+                    const uint32_t ma = __shfl_sync(0xffffffffu, b0, sm), mb = __shfl_sync(0xffffffffu, b1, sm);
+                    const uint32_t y0 = __shfl_sync(0xffffffffu, b0, sy), y1 = __shfl_sync(0xffffffffu, b1, sy);
+                    const uint32_t z0 = __shfl_sync(0xffffffffu, t0, sy), z1 = __shfl_sync(0xffffffffu, t1, sy);
+                    const uint32_t mk = (t & 1) ? mb : ma;
+                    if (lane == t) fv = f;
+                    if (rk && k > t) {
+                        if (ja > t) b0 = ff<MONT>(f, b0, mk, y0, M);
+                        if (jb > t) b1 = ff<MONT>(f, b1, mk, y1, M);
+                        t0 = ff<MONT>(f, t0, mk, z0, M);
+                        t1 = ff<MONT>(f, t1, mk, z1, M);
+                    }
+                }
+                if (ok) {
+                    if (rk && ja < np) W[(p0 + k) * PIV_LDW + r0 + ja] = b0;
+                    if (rk && jb < np) W[(p0 + k) * PIV_LDW + r0 + jb] = b1;
+                    if (rk) { s_T[k][ja] = t0; s_T[k][jb] = t1; }
+                    if (lane < np) {
+                        s_f[r0 + lane] = fv;
+                        s_pos[r0 + lane] = (r0 + lane == 0 && ext0 >= 0) ? ext0 : r0 + lane;
+                        s_prof[r0 + lane] = p0 + lane;
+                    }
+                    uint32_t S = Sprod;
+                    for (int t = 0; t < np; ++t) {
+                        const uint32_t ft = __shfl_sync(0xffffffffu, fv, t);
+                        if (lane == 0) s_Sfwd[r0 + t] = S;
+                        S = scale_mul<MONT>(S, ft, M);
+                    }
+                    if (lane == 0) s_sprod = S;
+                }
+                if (lane == 0) s_fast = ok ? 1 : 0;
+            }
+            __syncthreads();
+            fast = s_fast != 0;
+            try_fast = fast;
+        }
+        if (fast) {
+            // window positions right of the block, then E columns [0, pend): thread per column,
+            // panel rows 1 .. np-1 as sums of T's entries times the rows' values before the panel
+            const int nwc = wne - (r0 + np), ncol = nwc + pend;
+            for (int ci = tid; ci < ncol; ci += nt) {
+                const bool inw = ci < nwc;
+                uint32_t *base = inw ? W + r0 + np + ci : E + (ci - nwc);
+                const int st = inw ? PIV_LDW : PIV_LDE;
+                uint32_t x[PIV_PB];
+#pragma unroll
+                for (int j = 0; j < PIV_PB; ++j) x[j] = j < np ? base[(p0 + j) * st] : 0u;
+#pragma unroll
+                for (int kk = 1; kk < PIV_PB; ++kk) {
+                    if (kk < np) {
+                        uint64_t s0 = 0, s1 = 0;      // at most four products below 2^62 in each
+#pragma unroll
+                        for (int j = 0; j <= kk; ++j) {
+                            if (j < 4) s0 += (uint64_t)s_T[kk][j] * x[j];
+                            else s1 += (uint64_t)s_T[kk][j] * x[j];
+                        }
+                        base[(p0 + kk) * st] = addm(red64(s0, M), red64(s1, M), M);
+                    }
+                }
+            }
+            __syncthreads();
+            r = r0 + np;
+            Sprod = s_sprod;
+        } else {
         if (warp < PIV_PW) {
             // Panel of rows [p0, pend), eliminated by the first PIV_PW warps (named
             // barrier 1): the rows are taken one by one as in the unblocked
@@ -244,10 +334,11 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
             }
         }
         __syncthreads();
-        const int lim = s_state[pc & 1][4];
+        lim = s_state[pc & 1][4];
         r = s_state[pc & 1][0]; stop = s_state[pc & 1][1]; nspec = s_state[pc & 1][2];
         done = s_state[pc & 1][3] != 0;
-        const bool pswap = s_state[pc & 1][5] != 0;
+        pswap = s_state[pc & 1][5] != 0;
+        }
         const int bp = r - r0;
         if (bp == 0 || pend >= lim) continue;
         // Rows [pend, lim) take the panel's transpositions, then its bp pivots
