@@ -500,6 +500,18 @@ def run_ours(args):
         rst = h.stats()
         rstep_ms = sum(a.elapsed_time(b) for a, b in revs)
         h.set_option(cup.OPT_PROFILE, 0)
+    gathered = None
+    if batched:
+        # each rank's per-matrix results (rank, det, row rank profile), gathered on the host
+        restore()
+        rk, prs, _, dts = h.factor_batched(work, primes, want_det=True)
+        torch.cuda.synchronize()
+        rk, dts = rk.cpu().numpy().tolist(), dts.cpu().numpy().view(np.uint32).tolist()
+        recs = [[rk[i], dts[i] if mats[i][0].shape[0] == mats[i][0].shape[1] else None,
+                 prs[i][:rk[i]].cpu().numpy().tolist()] for i in range(len(mats))]
+        allrec = gather_batched(count_all, shard, recs, world)
+        gathered = {"matrices": len(allrec), "ranks": world, "rank_sum": int(sum(r[0] for r in allrec)),
+                    "square_dets": sum(1 for r in allrec if r[1] is not None)}
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, world)
     # replicas: every rank did the same work; a sharded batch: each rank its share
@@ -527,6 +539,8 @@ def run_ours(args):
                               "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}, **shape),
               "gpu_launches": int(st["launches"]),
               "clocks": clk}
+    if gathered:
+        result["batch_gather"] = gathered
 
     peaks = {}
     try:

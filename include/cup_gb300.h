@@ -101,6 +101,21 @@ cup_status cup_destroy(cup_handle *handle);
 /* Set an option (see the CUP_OPT_* list). */
 cup_status cup_set_option(cup_handle *handle, int option, int64_t value);
 
+/* Tuning table of the schedule options (no counterpart in the paper: the
+ * recursion's leaf size, the base case's pivot window and the smallest inner
+ * dimension sent to the tensor engine only change how fast a factorization
+ * runs, never its result). `table` is JSON text {"entries": [rule, ...]}; each
+ * rule is an object with numeric fields: the keys "limbs" (1..4, the tensor
+ * engine's limb count of p), "tall" (1: m >= 2n, 0: otherwise), "min_lo" and
+ * "min_hi" (min(m, n) in [min_lo, min_hi)) select calls (an absent key matches
+ * every call), and "leaf_rows", "window", "tc_min_k" give the options. Each
+ * factorization (cup_factor and every call built on it) takes the first rule
+ * that matches; options set with cup_set_option take precedence. Other keys
+ * (timings, notes) are ignored. NULL clears the table. The text is parsed and
+ * copied: CUP_ERR_ARG if it is malformed (the previous table is kept). The
+ * tuner paper_1112_5717_gb300/tune.py writes such a table from measured times. */
+cup_status cup_set_tuning(cup_handle *handle, const char *table);
+
 /* Text of the last CUDA error seen by this handle (static storage). */
 const char *cup_last_cuda_error(cup_handle *handle);
 

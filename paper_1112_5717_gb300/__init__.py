@@ -18,6 +18,8 @@ __all__ = ["load", "Handle", "factor", "rank_profile", "det", "inverse", "rref",
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcup_gb300.so")
+# schedule options measured by tune.py on the GB300, loaded into every handle by default
+TUNING_PATH = os.path.join(_HERE, "tuning.json")
 
 ENGINE_PLAIN = 0
 ENGINE_TENSOR = 1
@@ -83,6 +85,7 @@ SIGNATURES = {
     "cup_mm_sub_noalloc": (_INT, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _U32, _P]),
     "cup_factor_batched": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "cup_selftest_wait": (_INT, [_P, _I64, _P]),
+    "cup_set_tuning": (_INT, [_P, ctypes.c_char_p]),
     "cup_factor_u8": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_factor_host_u8": (_INT, [_P, _P, _I64, _P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_det_u8": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
@@ -174,7 +177,9 @@ def _from_words(words, nwords: int, sign: int) -> int:
 class Handle:
     """Owns a cup_handle (and its device workspace) for one CUDA device."""
 
-    def __init__(self, device: int | None = None, engine: int | None = None, **opts):
+    def __init__(self, device: int | None = None, engine: int | None = None, tuning=None, **opts):
+        """tuning: None loads the tuning table next to the library (if present), a str is a
+        table's JSON text or a path to one, False loads none."""
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the CUP library has no CPU path")
@@ -183,6 +188,11 @@ class Handle:
         h = ctypes.c_void_p()
         self._check(self.lib.cup_create(ctypes.byref(h), self.device), "cup_create", None)
         self.h = h
+        if tuning is None and os.path.exists(TUNING_PATH):
+            tuning = TUNING_PATH
+        if tuning:
+            text = open(tuning).read() if os.path.exists(tuning) else tuning
+            self._check(self.lib.cup_set_tuning(self.h, text.encode()), "cup_set_tuning", self.h)
         if engine is not None:
             self.set_option(OPT_ENGINE, engine)
         names = {"leaf_rows": OPT_LEAF_ROWS, "window": OPT_WINDOW, "tc_min_k": OPT_TC_MIN_K,

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <new>
+#include <string>
 #include <vector>
 #include "cup_internal.cuh"
 #include "../../include/cup_gb300.h"
@@ -31,6 +32,12 @@ struct cup_handle {
     int leaf_rows = 64;
     int window = 96;
     int64_t tc_min_k = 64;
+    bool user_set[3] = {false, false, false};   // leaf_rows, window, tc_min_k set by cup_set_option
+    struct TuneRule {
+        int64_t limbs = -1, tall = -1, min_lo = 0, min_hi = INT64_MAX;
+        int64_t leaf_rows = 0, window = 0, tc_min_k = 0;
+    };
+    std::vector<TuneRule> tuning;  // from cup_set_tuning: the first matching rule applies
     int validate = 0;
     SlabScratch *d_slab = nullptr;
     int2 *d_pairs = nullptr;
@@ -992,9 +999,38 @@ cup_status ensure_wide(cup_handle *h, size_t bytes)
 // fallback when a row taken as dependent was not), which first loads the input
 // again: from the host, from the device bytes, or from the backup copy that the
 // device-resident run made of a uint32 device input.
+// The handle's schedule options for one factorization: the first rule of the tuning
+// table that matches the call's limb count and shape sets those the caller did not set
+// with cup_set_option; the handle's own values come back when the call returns.
+struct TunedOptions {
+    cup_handle *h;
+    int leaf_rows, window;
+    int64_t tc_min_k;
+    TunedOptions(cup_handle *h_, int64_t m, int64_t n, uint32_t p)
+        : h(h_), leaf_rows(h_->leaf_rows), window(h_->window), tc_min_k(h_->tc_min_k)
+    {
+        const int64_t L = tc_limbs(p), k = m < n ? m : n, tall = m >= 2 * n ? 1 : 0;
+        for (const auto &r : h->tuning) {
+            if ((r.limbs >= 0 && r.limbs != L) || (r.tall >= 0 && r.tall != tall) || k < r.min_lo || k >= r.min_hi)
+                continue;
+            if (!h->user_set[0] && r.leaf_rows >= 1 && r.leaf_rows <= CUP_BMAX) h->leaf_rows = (int)r.leaf_rows;
+            if (!h->user_set[1] && r.window >= 1 && r.window <= CUP_WNMAX) h->window = (int)r.window;
+            if (!h->user_set[2] && r.tc_min_k >= 1) h->tc_min_k = r.tc_min_k;
+            break;
+        }
+    }
+    ~TunedOptions()
+    {
+        h->leaf_rows = leaf_rows;
+        h->window = window;
+        h->tc_min_k = tc_min_k;
+    }
+};
+
 cup_status factor_impl(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
                        int64_t *d_profile, int64_t *d_ipiv, int64_t *rank, cudaStream_t st, const InputSrc &src)
 {
+    TunedOptions tuned(h, m, n, p);
     cup_status s = CUP_ERR_SPECULATION_INTERNAL;
     if (h->schedule == 1) s = factor_device(h, A, m, n, lda, p, d_profile, d_ipiv, rank, st, src);
     if (s != CUP_ERR_SPECULATION_INTERNAL) return s;
@@ -1127,14 +1163,17 @@ cup_status cup_set_option(cup_handle *h, int option, int64_t value)
     case CUP_OPT_LEAF_ROWS:
         if (value < 1 || value > CUP_BMAX) return CUP_ERR_ARG;
         h->leaf_rows = (int)value;
+        h->user_set[0] = true;
         return CUP_OK;
     case CUP_OPT_WINDOW:
         if (value < 1 || value > CUP_WNMAX) return CUP_ERR_ARG;
         h->window = (int)value;
+        h->user_set[1] = true;
         return CUP_OK;
     case CUP_OPT_TC_MIN_K:
         if (value < 1) return CUP_ERR_ARG;
         h->tc_min_k = value;
+        h->user_set[2] = true;
         return CUP_OK;
     case CUP_OPT_VALIDATE:
         h->validate = value != 0;
@@ -1683,6 +1722,98 @@ cup_status cup_trlum(cup_handle *h, uint32_t *A, int64_t lda, int64_t n, uint32_
     CK(ensure_base(h));
     CK(trlum(h, A, lda, n, 1, make_modp(p), h->engine, (cudaStream_t)stream));
     CK(check_device_error(h, (cudaStream_t)stream));
+    return CUP_OK;
+}
+
+// Reads the tuning table {"entries": [{"key": number, ...}, ...]}: every object of the
+// entries array is one rule; numbers are read as integers (fractions dropped), string,
+// array and object values are skipped, unknown keys are ignored.
+static bool parse_tuning(const char *t, std::vector<cup_handle::TuneRule> &out)
+{
+    const char *e = strstr(t, "\"entries\"");
+    if (!e) return false;
+    const char *c = strchr(e, '[');
+    if (!c) return false;
+    ++c;
+    auto ws = [&]() { while (*c == ' ' || *c == '\n' || *c == '\r' || *c == '\t' || *c == ',') ++c; };
+    auto skip_value = [&]() -> bool {
+        if (*c == '"') {
+            for (++c; *c && *c != '"'; ++c)
+                if (*c == '\\' && c[1]) ++c;
+            if (!*c) return false;
+            ++c;
+            return true;
+        }
+        if (*c == '[' || *c == '{') {
+            int depth = 0;
+            bool str = false;
+            for (; *c; ++c) {
+                if (str) { if (*c == '\\' && c[1]) ++c; else if (*c == '"') str = false; continue; }
+                if (*c == '"') str = true;
+                else if (*c == '[' || *c == '{') ++depth;
+                else if ((*c == ']' || *c == '}') && --depth == 0) { ++c; return true; }
+            }
+            return false;
+        }
+        for (const char *lit : {"true", "false", "null"}) {
+            const size_t k = strlen(lit);
+            if (strncmp(c, lit, k) == 0) {
+                c += k;
+                return true;
+            }
+        }
+        return false;
+    };
+    for (;;) {
+        ws();
+        if (*c == ']') return true;
+        if (*c != '{') return false;
+        ++c;
+        cup_handle::TuneRule r;
+        for (;;) {
+            ws();
+            if (*c == '}') { ++c; break; }
+            if (*c != '"') return false;
+            const char *k0 = ++c;
+            while (*c && *c != '"') ++c;
+            if (!*c) return false;
+            const std::string key(k0, (size_t)(c - k0));
+            ++c;
+            ws();
+            if (*c != ':') return false;
+            ++c;
+            ws();
+            if (*c == '-' || (*c >= '0' && *c <= '9')) {
+                char *endp = nullptr;
+                const double v = strtod(c, &endp);
+                if (endp == c) return false;
+                c = endp;
+                const int64_t iv = (int64_t)v;
+                if (key == "limbs") r.limbs = iv;
+                else if (key == "tall") r.tall = iv;
+                else if (key == "min_lo") r.min_lo = iv;
+                else if (key == "min_hi") r.min_hi = iv;
+                else if (key == "leaf_rows") r.leaf_rows = iv;
+                else if (key == "window") r.window = iv;
+                else if (key == "tc_min_k") r.tc_min_k = iv;
+            } else if (!skip_value()) {
+                return false;
+            }
+        }
+        out.push_back(r);
+    }
+}
+
+cup_status cup_set_tuning(cup_handle *h, const char *table)
+{
+    if (!h) return CUP_ERR_ARG;
+    if (!table) {
+        h->tuning.clear();
+        return CUP_OK;
+    }
+    std::vector<cup_handle::TuneRule> rules;
+    if (!parse_tuning(table, rules)) return CUP_ERR_ARG;
+    h->tuning.swap(rules);
     return CUP_OK;
 }
 

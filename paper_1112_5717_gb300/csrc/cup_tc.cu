@@ -30,6 +30,7 @@ constexpr int BK = 64;        // k per pipeline stage: one 128-byte swizzle row 
 constexpr int NEPI = 16;      // epilogue warps (four per TMEM lane quarter)
 constexpr int NTHREADS = 32 * (2 + NEPI);
 constexpr int SMEM_BUDGET = 200 * 1024;
+constexpr int GROUP_M = 16;   // tile rows walked together by consecutive CTAs
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -204,16 +205,23 @@ template <int L, int BNX = 0>
 struct Cfg {
     static constexpr int NACC = 2 * L - 1;
     static constexpr int BN = BNX ? BNX : ((NACC * 128 <= 512) ? 128 : 64);
+    // 256-column tiles keep the partial sums of earlier K chunks in the epilogue
+    // threads' registers (64 one-byte residues, four to a register) instead of TMEM,
+    // and do not prefetch C
+    static constexpr bool REGP = BN > 128;
+    static_assert(!REGP || L == 1, "register partial sums hold one-byte residues (p < 2^8)");
     // two accumulator sets (the MMAs of chunk c + 1 run while chunk c is drained) when
     // they fit in TMEM next to the partial sums
-    static constexpr int NBUF = (2 * NACC * BN + BN <= 512) ? 2 : 1;
+    static constexpr int NBUF = (2 * NACC * BN + (REGP ? 0 : BN) <= 512) ? 2 : 1;
     static constexpr int STAGE_A = BM * BK * 2;
     static constexpr int STAGE_B = BN * BK * 2;
     static constexpr int STAGE = L * (STAGE_A + STAGE_B);
     static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 8 ? (SMEM_BUDGET / STAGE) : 8;
-    static constexpr int CBUF = BM * BN * 4;                  // a C tile (prefetch when K is short)
+    static constexpr int CBUF = REGP ? 0 : BM * BN * 4;       // a C tile (prefetch when K is short)
     static constexpr int SMEMUSE = (NSTAGE * STAGE > (NSTAGE - 1) * STAGE + CBUF) ? NSTAGE * STAGE
                                                                                    : (NSTAGE - 1) * STAGE + CBUF;
+    static_assert(BM * BN * 4 <= NSTAGE * STAGE, "the staged result tile fits in the stage memory");
+    static_assert(NBUF * NACC * BN + (REGP ? 0 : BN) <= 512, "accumulators fit in TMEM");
     static constexpr int SMEM = SMEMUSE + 1024;
     static constexpr int KCHUNK = (1024 / L) / BK * BK;      // L * kc * 2^14 <= 2^24
     static constexpr int COLS_PER_WARP = BN / 2;
@@ -233,7 +241,15 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int add = d.add;
     const int64_t ldc = d.ldc;
     using CF = Cfg<L, BNX>;
-    if ((int)blockIdx.x * CF::BN >= N || K <= 0) {            // outside this call's extents
+    // Tile of this CTA: the grid is one-dimensional and walks groups of GROUP_M tile
+    // rows, tile row fastest within a group, so the CTAs resident at a time share a
+    // few A and B tiles (read from L2) instead of all of B's planes.
+    const int mt = (M + BM - 1) / BM, ntl = gridDim.x / mt;
+    const int id = blockIdx.x, grp = id / (GROUP_M * ntl), first = grp * GROUP_M;
+    const int gsz = (mt - first) < GROUP_M ? (mt - first) : GROUP_M;
+    const int inr = id - grp * GROUP_M * ntl;
+    const int tm = first + inr % gsz, tn = inr / gsz;
+    if (tn * CF::BN >= N || K <= 0) {                          // outside this call's extents
         pdl_enter();
         return;
     }
@@ -246,13 +262,13 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int m0 = tm * BM, n0 = tn * BN;
     const int nkb = Kp / BK;
     const int kb_chunk = CF::KCHUNK / BK;
     const int nchunk = (nkb + kb_chunk - 1) / kb_chunk;
     // a short K uses fewer stages; the C tile is then prefetched into the spare space
     const int nst = nkb < NSTAGE ? nkb : NSTAGE;
-    const bool pref = nkb < NSTAGE;
+    const bool pref = CF::CBUF > 0 && nkb < NSTAGE;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
@@ -381,6 +397,7 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t mu32 = (uint32_t)(Mp.mu >> 32);    // floor(2^32 / p) for odd p
         uint32_t *tile = (uint32_t *)smem;
         bool ok = true;
+        uint32_t runr[CF::REGP ? CPW / 4 : 1];            // partial sums of earlier chunks (REGP), packed bytes
         for (int c = 0; c < nchunk; ++c) {
             const int buf = c % NBUF;
             if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)(c / NBUF) & 1u, err, 5)) { ok = false; break; }
@@ -395,7 +412,10 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                 for (int s = 0; s < NACC; ++s) tmem_ld8(tbase + s * BN, d[s]);
                 uint32_t run[CW];
-                if (c > 0) {
+                if (CF::REGP) {
+#pragma unroll
+                    for (int e = 0; e < CW; ++e) run[e] = (runr[(cb * CW + e) >> 2] >> (8 * ((cb * CW + e) & 3))) & 255u;
+                } else if (c > 0) {
                     float rf[CW];
                     tmem_ld8(pbase, rf);
 #pragma unroll
@@ -430,13 +450,19 @@ k_limb_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     run[e] = (c > 0) ? addm(run[e], r, Mp) : r;
                 }
                 if (!last) {
-                    tmem_st8(pbase, run);
+                    if (CF::REGP) {
+#pragma unroll
+                        for (int e = 0; e < CW; e += 4)
+                            runr[(cb * CW + e) >> 2] = run[e] | run[e + 1] << 8 | run[e + 2] << 16 | run[e + 3] << 24;
+                    } else {
+                        tmem_st8(pbase, run);
+                    }
                 } else {
 #pragma unroll
                     for (int e = 0; e < CW; ++e) tile[srow * BN + ((col + e) ^ (srow & 31))] = run[e];
                 }
             }
-            if (!last) tmem_wait_st();
+            if (!last && !CF::REGP) tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
@@ -625,7 +651,9 @@ cudaError_t run_cfg(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t
     const int bound_bits = (L <= 3) ? 60 : 52;
     const uint64_t off = ((1ull << bound_bits) / Mp.p + 1) * Mp.p;
     const uint32_t sh32 = (uint32_t)((1ull << 32) % Mp.p);
-    dim3 grid((Nmax + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
+    const int64_t tiles = (int64_t)((Nmax + CF::BN - 1) / CF::BN) * ((M + BM - 1) / BM);
+    if (tiles > INT32_MAX) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)tiles);
     if (ev0) cudaEventRecord(ev0, st);
     cudaError_t e = launch_pdl(k_limb_gemm<L, BNX>, grid, NTHREADS, CF::SMEM, st, ta, tb, d, Mp, off, sh32, err);
     if (ev1) cudaEventRecord(ev1, st);
@@ -637,6 +665,10 @@ cudaError_t run_cfg(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t
 template <int L>
 cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
+    // one limb and a long K: 128 x 256 tiles read half again fewer operand bytes per product
+    if constexpr (L == 1) {
+        if (d.K.hi >= 1024) return run_cfg<L, 256>(d, Mp, ws, err, st, ev0, ev1);
+    }
     return run_cfg<L, 0>(d, Mp, ws, err, st, ev0, ev1);
 }
 

@@ -104,3 +104,57 @@ def test_operation_counts_follow_table_1():
     assert bench.op_ops("inplace_mm", n, n, n) == pytest.approx((2.0 / 3.0 + 2.0 + 2.0 / 3.0) * n ** 3)
     with pytest.raises(SystemExit):
         bench.op_ops("inverse", n, n, n - 1)
+
+
+_SHARD_WORKER = r"""
+import os, sys, json
+sys.path.insert(0, os.environ["CUP_ROOT"])
+import torch.distributed as dist
+import bench
+import oracle
+from paper_1112_5717_gb300 import inputs
+world = int(os.environ["WORLD_SIZE"])
+if world > 1:
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%s" % os.environ["MASTER_PORT"],
+                            rank=int(os.environ["RANK"]), world_size=world)
+world, rank, local = bench.dist_env()
+mats = inputs.batched(count=23, lo=8, hi=40, defect=6, seed=inputs.SEED_BASE + 77)
+idx = bench.shard_indices(len(mats), world, rank)
+recs = []
+for b in idx:
+    A, q = mats[b]
+    d = oracle.cup(A, q)
+    det = oracle.det(A, q) if A.shape[0] == A.shape[1] else None
+    recs.append([d["rank"], det, d["profile"].tolist()])
+out = bench.gather_batched(len(mats), idx, recs, world)
+print(json.dumps({"rank": rank, "idx": idx, "all": out}), flush=True)
+if world > 1:
+    dist.destroy_process_group()
+"""
+
+
+def test_batched_shard_and_gather_match_one_rank():
+    """The batched workload split across two gloo ranks (every other matrix, no data-path
+    collective; the oracle stands in for each rank's factor launch) and gathered on the
+    host gives, on both ranks, exactly the per-matrix results of one rank factoring all."""
+    one = _run_ranks(_SHARD_WORKER, 1)
+    two = _run_ranks(_SHARD_WORKER, 2)
+    for rc, out, err in one + two:
+        assert rc == 0, err
+    ref = json.loads(one[0][1].strip().splitlines()[-1])
+    got = [json.loads(o.strip().splitlines()[-1]) for _, o, _ in two]
+    assert ref["idx"] == list(range(23))
+    assert sorted(got[0]["idx"] + got[1]["idx"]) == list(range(23))
+    assert not set(got[0]["idx"]) & set(got[1]["idx"])
+    for g in got:
+        assert g["all"] == ref["all"]
+
+
+def test_gather_rejects_overlaps_and_gaps():
+    import bench
+    assert bench.gather_batched(3, [0, 1, 2], ["a", "b", "c"], 1) == ["a", "b", "c"]
+    with pytest.raises(RuntimeError):
+        bench.gather_batched(3, [0, 1], ["a", "b"], 1)
+    with pytest.raises(RuntimeError):
+        bench.gather_batched(2, [0, 0], ["a", "b"], 1)
+    assert bench.shard_indices(10, 3, 1) == [1, 4, 7]

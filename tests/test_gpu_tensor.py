@@ -41,7 +41,7 @@ def tensor_handle(cuda_lib):
 
 @pytest.mark.parametrize("p", PRIMES)
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 128, 64), (130, 77, 45), (200, 333, 600),
-                                   (257, 130, 1100), (64, 300, 2049)])
+                                   (257, 130, 1100), (64, 300, 2049), (300, 700, 4100)])
 def test_tensor_mm_sub_random(cuda_lib, tensor_handle, p, M, N, K):
     rng = np.random.default_rng((M * 31 + N * 7 + K) ^ (p & 0xFFFF))
     A = rng.integers(0, p, size=(M, K))
