@@ -74,6 +74,10 @@ def parse_args(argv=None):
                     help="extra untimed steps run with per-launch GEMM timing for the roofline object")
     ap.add_argument("--no-schur", action="store_true",
                     help="skip the isolated Schur-update measurement (16384^3 over GF(251))")
+    ap.add_argument("--schur-only", action="store_true",
+                    help="only the isolated Schur update (and the instruction probes), one JSON line")
+    ap.add_argument("--schur-n", type=int, default=16384, help="size of the isolated Schur update")
+    ap.add_argument("--no-probes", action="store_true", help="skip the tensor-instruction peak probes")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only warm-up and timed factorisations (for profiler launch lists)")
     return ap.parse_args(argv)
@@ -404,6 +408,19 @@ def run_ours(args):
     import paper_1112_5717_gb300 as cup
 
     world, rank, local = dist_env()
+    if args.schur_only:
+        torch.cuda.set_device(local)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        try:
+            peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            peaks = {}
+        out = measure_schur(cup, torch.cuda.current_device(), stream, peaks, n=args.schur_n,
+                            probes_on=not args.no_probes)
+        if rank == 0:
+            print(json.dumps({"schur": out}), flush=True)
+        return 0
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -569,7 +586,7 @@ def run_ours(args):
                               "achieved": rst["cc_field_flops"] / (rst["cc_ms"] * 1e-3) / 1e12,
                               "peak": None, "unit": "Tfield-op/s", "frac": None, "traffic": None}
     if world == 1 and not args.no_schur and not args.kernel_only:
-        result["schur"] = measure_schur(cup, dev, stream, peaks)
+        result["schur"] = measure_schur(cup, dev, stream, peaks, n=args.schur_n, probes_on=not args.no_probes)
     result["stats"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
     if args.profile >= 2:
         result["class_ms_per_step"] = {k: round(v / args.steps, 3) for k, v in h.class_ms().items() if v}
@@ -673,7 +690,8 @@ def captured_traffic(key: str):
     return rec["bytes_per_launch"], rec.get("capture", "ncu")
 
 
-def measure_schur(cup, dev, stream, peaks, n: int = 16384, p: int = 251, warm: int = 2, steps: int = 3):
+def measure_schur(cup, dev, stream, peaks, n: int = 16384, p: int = 251, warm: int = 2, steps: int = 3,
+                  probes_on: bool = True):
     """The Schur update C <- C - A B mod p alone at n^3 over GF(251) (one centred
     8-bit limb, the 32768^2 workload's update shape at n >= 16384), tensor engine:
     CUDA events on the library's stream around the tensor-core kernel only (the
@@ -700,6 +718,13 @@ def measure_schur(cup, dev, stream, peaks, n: int = 16384, p: int = 251, warm: i
             calls.append(e0.elapsed_time(e1))
     st = hs.stats()
     hs.close()
+    probes = {}
+    for kind, name in (((0, "int8_mma_sync_tops"), (1, "bf16_mma_sync_tflops"), (2, "tcgen05_f16_tflops"))
+                       if probes_on else ()):
+        try:
+            probes[name] = cup.probe_tensor_peak(kind, device=dev)
+        except Exception as e:                     # reported, not fatal to the benchmark line
+            probes[name] = f"failed: {e}"
     L = cup_limbs(p)
     kms = st["tc_ms"] / max(st["tc_launches"], 1)
     limb = 2.0 * L * L * n * n * n
@@ -710,7 +735,9 @@ def measure_schur(cup, dev, stream, peaks, n: int = 16384, p: int = 251, warm: i
             "kernel_ms": kms, "call_ms": statistics.mean(calls), "achieved": achieved, "unit": "TFLOP/s",
             "peak": peak, "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)" if peaks.get("bf16_tflops")
             else "fallback 1.9 PFLOP/s bf16", "frac": achieved / peak,
-            "field_tops": 2.0 * n * n * n / (kms * 1e-3) / 1e12}
+            "field_tops": 2.0 * n * n * n / (kms * 1e-3) / 1e12,
+            "instruction_peaks": probes,
+            "instruction_peaks_how": "cup_probe_tensor_peak: back-to-back instructions on resident operands, every SM"}
 
 
 def cup_limbs(p: int) -> int:

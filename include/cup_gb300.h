@@ -451,6 +451,20 @@ cup_status cup_mm_sub_noalloc(uint32_t *C, int64_t ldc, const uint32_t *A, int64
  * context stay usable. Synchronises `stream`. */
 cup_status cup_selftest_wait(cup_handle *handle, int64_t limit_us, void *stream);
 
+/* Peak-rate probe of a tensor instruction on CUDA device `device` (no
+ * counterpart in the paper: it measures the exact-integer tensor paths the
+ * library could use, to justify the choice of engine). Every SM runs `iters`
+ * iterations of back-to-back instructions on operands held in registers or
+ * shared memory; *tflops receives the rate in 10^12 operations per second
+ * (a multiply and an add count as two), from CUDA events around the launch
+ * after a shorter warm-up launch. kind 0: mma.sync m16n8k32 s8 x s8 -> s32;
+ * 1: mma.sync m16n8k16 bf16 -> f32; 2: tcgen05.mma kind::f16 with M = 128,
+ * N = 256, bf16 operands in shared memory and the fp32 accumulator in TMEM
+ * (the instruction of the tensor engine). Allocates and frees a few bytes;
+ * synchronises the device's work it launched. CUP_ERR_TIMEOUT if the bounded
+ * wait for the tcgen05 instructions expired. */
+cup_status cup_probe_tensor_peak(int device, int kind, int64_t iters, double *tflops);
+
 /* Column transpositions (Sec. 1.1): for t = k0..k1-1 in order, swap columns t
  * and d_ipiv[t] of rows row0..row0+nrows-1 of A (A <- A P^T restricted to
  * those transpositions). d_ipiv is a device array indexed by absolute

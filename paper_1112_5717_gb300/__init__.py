@@ -86,6 +86,7 @@ SIGNATURES = {
     "cup_factor_batched": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "cup_selftest_wait": (_INT, [_P, _I64, _P]),
     "cup_set_tuning": (_INT, [_P, ctypes.c_char_p]),
+    "cup_probe_tensor_peak": (_INT, [_INT, _INT, _I64, _DBLP]),
     "cup_factor_u8": (_INT, [_P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_factor_host_u8": (_INT, [_P, _P, _I64, _P, _P, _I64, _I64, _I64, _U32, _P, _P, _I64P, _P]),
     "cup_det_u8": (_INT, [_P, _P, _I64, _I64, _U32, _U32P, _P]),
@@ -601,6 +602,19 @@ def crt(residues, primes) -> int:
     if st != 0:
         raise CupError(st, "cup_crt", "")
     return _from_words(words, nw.value, sg.value)
+
+
+def probe_tensor_peak(kind: int, iters: int | None = None, device: int | None = None) -> float:
+    """Measured peak rate (10^12 ops/s) of a tensor instruction on this GPU:
+    kind 0 INT8 mma.sync, 1 bf16 mma.sync, 2 tcgen05.mma kind::f16 (cup_probe_tensor_peak)."""
+    torch = _torch()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    iters = iters or (20000 if kind == 2 else 4000)
+    out = ctypes.c_double(0.0)
+    st = load().cup_probe_tensor_peak(dev, int(kind), int(iters), ctypes.byref(out))
+    if st != 0:
+        raise CupError(st, "cup_probe_tensor_peak")
+    return out.value
 
 
 def primes_below(bound: int, count: int) -> list:

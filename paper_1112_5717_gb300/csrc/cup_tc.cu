@@ -672,7 +672,147 @@ cudaError_t run(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
     return run_cfg<L, 0>(d, Mp, ws, err, st, ev0, ev1);
 }
 
+// ---------------------------------------------------------------------------
+// Peak-rate probes of the tensor instructions an exact integer product could use
+// on this GPU (measurement support for the choice of engine; no counterpart in the
+// paper): back-to-back instructions on operands resident in registers or shared
+// memory, so each instruction's own rate is timed.
+//   kind 0: mma.sync m16n8k32 s8 x s8 -> s32 (8192 integer ops each)
+//   kind 1: mma.sync m16n8k16 bf16 x bf16 -> f32 (4096 flops each)
+//   kind 2: tcgen05.mma kind::f16, M = 128, N = 256, K = 16, bf16 operands in
+//           shared memory, fp32 accumulator in TMEM (1,048,576 flops each)
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(256) k_probe_mma_sync(int64_t iters, uint32_t *sink)
+{
+    const uint32_t s = threadIdx.x * 0x01010101u + 0x01020304u;
+    const uint32_t a[4] = {s, s ^ 0x11111111u, s ^ 0x22222222u, s ^ 0x33333333u};
+    const uint32_t b0 = s ^ 0x44444444u, b1 = s ^ 0x55555555u;
+    uint32_t c[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[j][e] = 0u;
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (KIND == 0)
+                asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                             "{%8,%9}, {%0,%1,%2,%3};"
+                             : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+                             : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+            else
+                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                             "{%8,%9}, {%0,%1,%2,%3};"
+                             : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+                             : "r"(a[0] & 0x3f803f80u), "r"(a[1] & 0x3f803f80u), "r"(a[2] & 0x3f803f80u),
+                               "r"(a[3] & 0x3f803f80u), "r"(b0 & 0x3f803f80u), "r"(b1 & 0x3f803f80u));
+        }
+    }
+    uint32_t x = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x ^= c[j][e];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+__global__ void __launch_bounds__(128, 1) k_probe_tcgen05(int64_t iters, int *err)
+{
+    extern __shared__ uint8_t praw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_sh;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)praw + 1023) & ~(uintptr_t)1023);
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = 256 * BK * 2;
+    for (int i = threadIdx.x; i < (A_BYTES + B_BYTES) / 16; i += blockDim.x) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes, read by the tensor core
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+    if (threadIdx.x == 0) {
+        constexpr uint32_t idesc = idesc_bf16(256);
+        const uint32_t sa = smem_u32(smem), sb = sa + A_BYTES;
+        for (int64_t it = 0; it < iters; ++it)
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc, (it | kk) ? 1u : 0u);
+        mma_commit(smem_u32(&bar));
+        mbar_wait(smem_u32(&bar), 0u, err, 98);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+}
+
 }  // namespace tc
+
+extern "C" cup_status cup_probe_tensor_peak(int device, int kind, int64_t iters, double *tflops)
+{
+    if (!tflops || kind < 0 || kind > 2 || iters < 1 || iters > (int64_t)1 << 30) return CUP_ERR_ARG;
+    *tflops = 0.0;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return CUP_ERR_ARG;
+    int nsm = 0;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int *err = nullptr;
+    uint32_t *sink = nullptr;
+    cup_status s = CUP_OK;
+    float ms = 0.f;
+    // the tcgen05 probe asks for more shared memory than two CTAs could share, so each
+    // SM runs one (its operand tiles take 49 KB of it)
+    const size_t psmem = 120 * 1024;
+    const int nthr = kind == 2 ? 128 : 256;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&sink, (size_t)nsm * 2 * 256 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+        (kind == 2 && cudaFuncSetAttribute(tc::k_probe_tcgen05, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)psmem) != cudaSuccess)) {
+        s = CUP_ERR_CUDA;
+    }
+    const int grid = kind == 2 ? nsm : 2 * nsm;
+    for (int rep = 0; rep < 2 && s == CUP_OK; ++rep) {       // the first launch warms up
+        const int64_t n = rep ? iters : (iters + 9) / 10;
+        cudaEventRecord(e0, st);
+        if (kind == 0) tc::k_probe_mma_sync<0><<<grid, nthr, 0, st>>>(n, sink);
+        else if (kind == 1) tc::k_probe_mma_sync<1><<<grid, nthr, 0, st>>>(n, sink);
+        else tc::k_probe_tcgen05<<<grid, nthr, psmem, st>>>(n, err);
+        cudaEventRecord(e1, st);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) s = CUP_ERR_CUDA;
+        if (s == CUP_OK && rep) {
+            if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f) s = CUP_ERR_CUDA;
+            const double per = kind == 0 ? 8.0 * 8192.0 * (nthr / 32) : kind == 1 ? 8.0 * 4096.0 * (nthr / 32)
+                                                                         : 4.0 * 2.0 * tc::BM * 256.0 * 16.0;
+            if (s == CUP_OK) *tflops = per * (double)grid * (double)n / (ms * 1e-3) / 1e12;
+        }
+    }
+    int herr = 0;
+    if (s == CUP_OK && cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && herr)
+        s = CUP_ERR_TIMEOUT;
+    if (sink) cudaFree(sink);
+    if (err) cudaFree(err);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
 
 cudaError_t launch_selftest_wait(int *err, uint64_t limit_ns, int code, cudaStream_t st)
 {
