@@ -115,7 +115,7 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     __shared__ int s_wcol[CUP_WNMAX];
     __shared__ int s_prof[CUP_BMAX], s_pos[CUP_BMAX], s_spec[CUP_BMAX];
     __shared__ uint32_t s_f[CUP_BMAX], s_finv[CUP_BMAX], s_muinv[CUP_BMAX], s_Sinv[CUP_BMAX],
-        s_Sfwd[CUP_BMAX];
+        s_Sfwd[CUP_BMAX], s_Spinv[CUP_BMAX + 1];
     __shared__ __align__(16) uint32_t s_coef[CUP_BMAX][PIV_PB];   // -a_kt of the block update, per row below a panel
     __shared__ int s_c, s_ext, s_fast;
     __shared__ int s_state[2][6];              // after each panel: rank, stop, spec count, done, rows to update, swaps
@@ -185,32 +185,36 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         // columns, instead of np steps separated by barriers. A zero on the diagonal sends
         // this panel, and the rest of the slab, to the stepwise elimination below.
         bool fast = false;
-        if (try_fast && r0 + np <= wne) {
+        if (try_fast && np == PIV_PB && r0 + np <= wne) {
             if (warp == 0) {
                 const int k = lane >> 2, jg = lane & 3, ja = 2 * jg, jb = ja + 1;
-                const bool rk = k < np;
-                uint32_t b0 = (rk && ja < np) ? W[(p0 + k) * PIV_LDW + r0 + ja] : 0u;
-                uint32_t b1 = (rk && jb < np) ? W[(p0 + k) * PIV_LDW + r0 + jb] : 0u;
+                const bool rk = true;
+                uint32_t b0 = W[(p0 + k) * PIV_LDW + r0 + ja];
+                uint32_t b1 = W[(p0 + k) * PIV_LDW + r0 + jb];
                 uint32_t t0 = (k == ja) ? one : 0u, t1 = (k == jb) ? one : 0u;
                 uint32_t fv = 0u;                     // lane t keeps the pivot of step t
-                bool ok = true;
-                for (int t = 0; t < np; ++t) {
+                bool zero = false;
+                // all eight steps unrolled; a zero pivot (the same value in every lane) is
+                // noted and the block's results are then discarded
+#pragma unroll
+                for (int t = 0; t < PIV_PB; ++t) {
                     const int sf = 4 * t + (t >> 1), sm = 4 * k + (t >> 1), sy = 4 * t + jg;
                     const uint32_t fa = __shfl_sync(0xffffffffu, b0, sf), fb = __shfl_sync(0xffffffffu, b1, sf);
                     const uint32_t f = (t & 1) ? fb : fa;
-                    if (f == 0u) { ok = false; break; }      // the same value in every lane
+                    zero |= f == 0u;
                     const uint32_t ma = __shfl_sync(0xffffffffu, b0, sm), mb = __shfl_sync(0xffffffffu, b1, sm);
                     const uint32_t y0 = __shfl_sync(0xffffffffu, b0, sy), y1 = __shfl_sync(0xffffffffu, b1, sy);
                     const uint32_t z0 = __shfl_sync(0xffffffffu, t0, sy), z1 = __shfl_sync(0xffffffffu, t1, sy);
                     const uint32_t mk = (t & 1) ? mb : ma;
                     if (lane == t) fv = f;
-                    if (rk && k > t) {
+                    if (k > t) {
                         if (ja > t) b0 = ff<MONT>(f, b0, mk, y0, M);
                         if (jb > t) b1 = ff<MONT>(f, b1, mk, y1, M);
                         t0 = ff<MONT>(f, t0, mk, z0, M);
                         t1 = ff<MONT>(f, t1, mk, z1, M);
                     }
                 }
+                const bool ok = !zero;
                 if (ok) {
                     if (rk && ja < np) W[(p0 + k) * PIV_LDW + r0 + ja] = b0;
                     if (rk && jb < np) W[(p0 + k) * PIV_LDW + r0 + jb] = b1;
@@ -221,7 +225,8 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                         s_prof[r0 + lane] = p0 + lane;
                     }
                     uint32_t S = Sprod;
-                    for (int t = 0; t < np; ++t) {
+#pragma unroll
+                    for (int t = 0; t < PIV_PB; ++t) {
                         const uint32_t ft = __shfl_sync(0xffffffffu, fv, t);
                         if (lane == 0) s_Sfwd[r0 + t] = S;
                         S = scale_mul<MONT>(S, ft, M);
@@ -478,32 +483,18 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     }
     const int rs = r;
 
-    // Row scale of step t: mu_t = f_t (R^{-1} f_t in the Montgomery variant).
-    for (int t = tid; t < rs; t += nt) {
-        const uint32_t mu = MONT ? redc((uint64_t)s_f[t], M) : s_f[t];
-        const uint32_t muinv = inv_any<MONT>(mu, M);
-        s_muinv[t] = muinv;
-        s_finv[t] = MONT ? redc((uint64_t)muinv, M) : muinv;   // f^{-1} = mu^{-1} R^{-1}
-    }
+    // Row scales: step t multiplied the rows below its pivot row by mu_t = f_t (R^{-1} f_t in
+    // the Montgomery variant), and s_Sfwd[t] = prod_{t' < t} mu_t' (Sprod is the whole
+    // product). One parallel pass inverts every prefix product; mu_t^{-1} =
+    // Sfwd[t] / Sfwd[t + 1] is then a single product, so no prefix scan is needed. For odd p
+    // Sinv is kept in Montgomery representation (Sinv R), as the C values below expect.
+    for (int t = tid; t <= rs; t += nt) s_Spinv[t] = inv_any<MONT>(t < rs ? s_Sfwd[t] : Sprod, M);
     __syncthreads();
-    if (warp == 0) {
-        // exclusive prefix products Sinv[t] = prod_{t' < t} mu_{t'}^{-1}; for odd p kept in
-        // Montgomery representation (Sinv R), products by Montgomery steps
-        const uint32_t oneR = MONT ? redc((uint64_t)M.r2, M) : one;
-        uint32_t carry = oneR;
-        for (int base = 0; base < rs; base += 32) {
-            const int t = base + lane;
-            uint32_t v = (t < rs) ? (MONT ? redc((uint64_t)s_muinv[t] * M.r2, M) : s_muinv[t]) : oneR;
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v = MONT ? redc((uint64_t)v * u, M) : mulm(v, u, M);
-            }
-            uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
-            if (lane == 0) ex = oneR;
-            if (t < rs) s_Sinv[t] = MONT ? redc((uint64_t)carry * ex, M) : mulm(carry, ex, M);
-            const uint32_t last = __shfl_sync(0xffffffffu, v, 31);
-            carry = MONT ? redc((uint64_t)carry * last, M) : mulm(carry, last, M);
-        }
+    for (int t = tid; t < rs; t += nt) {
+        const uint32_t muinv = mulm(s_Sfwd[t], s_Spinv[t + 1], M);
+        s_muinv[t] = muinv;
+        s_Sinv[t] = MONT ? redc((uint64_t)s_Spinv[t] * M.r2, M) : s_Spinv[t];
+        s_finv[t] = MONT ? redc((uint64_t)muinv, M) : muinv;   // f^{-1} = mu^{-1} R^{-1}
     }
     __syncthreads();
 
