@@ -171,6 +171,60 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     int r = 0, stop = brows, nspec = 0, pc = 0;
     bool done = false, try_fast = true;
     uint32_t Sprod = one;                      // product of the row scales applied so far (every thread)
+    bool pre_done = false;                     // this panel's block was eliminated during the last update
+    // Warp 0's part of the fast panel path (see below) for the panel of rows [bp0, bp0 + 8)
+    // at rank position br0: the fraction-free steps on the 8 x 8 diagonal block in registers,
+    // T, the pivots and the running scale; s_fast = 1 when no pivot was zero (otherwise
+    // nothing but s_fast is written).
+    auto block_elim = [&](const int bp0, const int br0) {
+        const int k = lane >> 2, jg = lane & 3, ja = 2 * jg, jb = ja + 1;
+        uint32_t b0 = W[(bp0 + k) * PIV_LDW + br0 + ja];
+        uint32_t b1 = W[(bp0 + k) * PIV_LDW + br0 + jb];
+        uint32_t t0 = (k == ja) ? one : 0u, t1 = (k == jb) ? one : 0u;
+        uint32_t fv = 0u;                     // lane t keeps the pivot of step t
+        bool zero = false;
+        // all eight steps unrolled; a zero pivot (the same value in every lane) is
+        // noted and the block's results are then discarded
+#pragma unroll
+        for (int t = 0; t < PIV_PB; ++t) {
+            const int sf = 4 * t + (t >> 1), sm = 4 * k + (t >> 1), sy = 4 * t + jg;
+            const uint32_t fa = __shfl_sync(0xffffffffu, b0, sf), fb = __shfl_sync(0xffffffffu, b1, sf);
+            const uint32_t f = (t & 1) ? fb : fa;
+            zero |= f == 0u;
+            const uint32_t ma = __shfl_sync(0xffffffffu, b0, sm), mb = __shfl_sync(0xffffffffu, b1, sm);
+            const uint32_t y0 = __shfl_sync(0xffffffffu, b0, sy), y1 = __shfl_sync(0xffffffffu, b1, sy);
+            const uint32_t z0 = __shfl_sync(0xffffffffu, t0, sy), z1 = __shfl_sync(0xffffffffu, t1, sy);
+            const uint32_t mk = (t & 1) ? mb : ma;
+            if (lane == t) fv = f;
+            if (k > t) {
+                if (ja > t) b0 = ff<MONT>(f, b0, mk, y0, M);
+                if (jb > t) b1 = ff<MONT>(f, b1, mk, y1, M);
+                t0 = ff<MONT>(f, t0, mk, z0, M);
+                t1 = ff<MONT>(f, t1, mk, z1, M);
+            }
+        }
+        const bool ok = !zero;
+        if (ok) {
+            W[(bp0 + k) * PIV_LDW + br0 + ja] = b0;
+            W[(bp0 + k) * PIV_LDW + br0 + jb] = b1;
+            s_T[k][ja] = t0;
+            s_T[k][jb] = t1;
+            if (lane < PIV_PB) {
+                s_f[br0 + lane] = fv;
+                s_pos[br0 + lane] = (br0 + lane == 0 && ext0 >= 0) ? ext0 : br0 + lane;
+                s_prof[br0 + lane] = bp0 + lane;
+            }
+            uint32_t S = Sprod;
+#pragma unroll
+            for (int t = 0; t < PIV_PB; ++t) {
+                const uint32_t ft = __shfl_sync(0xffffffffu, fv, t);
+                if (lane == 0) s_Sfwd[br0 + t] = S;
+                S = scale_mul<MONT>(S, ft, M);
+            }
+            if (lane == 0) s_sprod = S;
+        }
+        if (lane == 0) s_fast = ok ? 1 : 0;
+    };
     for (; p0 < brows && !done; p0 += PIV_PB, ++pc) {
         const int pend = p0 + PIV_PB < brows ? p0 + PIV_PB : brows;
         const int r0 = r, np = pend - p0;
@@ -185,56 +239,13 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         // columns, instead of np steps separated by barriers. A zero on the diagonal sends
         // this panel, and the rest of the slab, to the stepwise elimination below.
         bool fast = false;
-        if (try_fast && np == PIV_PB && r0 + np <= wne) {
-            if (warp == 0) {
-                const int k = lane >> 2, jg = lane & 3, ja = 2 * jg, jb = ja + 1;
-                const bool rk = true;
-                uint32_t b0 = W[(p0 + k) * PIV_LDW + r0 + ja];
-                uint32_t b1 = W[(p0 + k) * PIV_LDW + r0 + jb];
-                uint32_t t0 = (k == ja) ? one : 0u, t1 = (k == jb) ? one : 0u;
-                uint32_t fv = 0u;                     // lane t keeps the pivot of step t
-                bool zero = false;
-                // all eight steps unrolled; a zero pivot (the same value in every lane) is
-                // noted and the block's results are then discarded
-#pragma unroll
-                for (int t = 0; t < PIV_PB; ++t) {
-                    const int sf = 4 * t + (t >> 1), sm = 4 * k + (t >> 1), sy = 4 * t + jg;
-                    const uint32_t fa = __shfl_sync(0xffffffffu, b0, sf), fb = __shfl_sync(0xffffffffu, b1, sf);
-                    const uint32_t f = (t & 1) ? fb : fa;
-                    zero |= f == 0u;
-                    const uint32_t ma = __shfl_sync(0xffffffffu, b0, sm), mb = __shfl_sync(0xffffffffu, b1, sm);
-                    const uint32_t y0 = __shfl_sync(0xffffffffu, b0, sy), y1 = __shfl_sync(0xffffffffu, b1, sy);
-                    const uint32_t z0 = __shfl_sync(0xffffffffu, t0, sy), z1 = __shfl_sync(0xffffffffu, t1, sy);
-                    const uint32_t mk = (t & 1) ? mb : ma;
-                    if (lane == t) fv = f;
-                    if (k > t) {
-                        if (ja > t) b0 = ff<MONT>(f, b0, mk, y0, M);
-                        if (jb > t) b1 = ff<MONT>(f, b1, mk, y1, M);
-                        t0 = ff<MONT>(f, t0, mk, z0, M);
-                        t1 = ff<MONT>(f, t1, mk, z1, M);
-                    }
-                }
-                const bool ok = !zero;
-                if (ok) {
-                    if (rk && ja < np) W[(p0 + k) * PIV_LDW + r0 + ja] = b0;
-                    if (rk && jb < np) W[(p0 + k) * PIV_LDW + r0 + jb] = b1;
-                    if (rk) { s_T[k][ja] = t0; s_T[k][jb] = t1; }
-                    if (lane < np) {
-                        s_f[r0 + lane] = fv;
-                        s_pos[r0 + lane] = (r0 + lane == 0 && ext0 >= 0) ? ext0 : r0 + lane;
-                        s_prof[r0 + lane] = p0 + lane;
-                    }
-                    uint32_t S = Sprod;
-#pragma unroll
-                    for (int t = 0; t < PIV_PB; ++t) {
-                        const uint32_t ft = __shfl_sync(0xffffffffu, fv, t);
-                        if (lane == 0) s_Sfwd[r0 + t] = S;
-                        S = scale_mul<MONT>(S, ft, M);
-                    }
-                    if (lane == 0) s_sprod = S;
-                }
-                if (lane == 0) s_fast = ok ? 1 : 0;
-            }
+        if (pre_done) {
+            // warp 0 eliminated this panel's block while the others finished the last update
+            fast = s_fast != 0;
+            try_fast = fast;
+            pre_done = false;
+        } else if (try_fast && np == PIV_PB && r0 + np <= wne) {
+            if (warp == 0) block_elim(p0, r0);
             __syncthreads();
             fast = s_fast != 0;
             try_fast = fast;
@@ -263,7 +274,12 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                     }
                 }
             }
-            __syncthreads();
+            // With rows below the panel the block update's multiplier pass runs next without a
+            // barrier: it reads those rows and the pivot rows at the block's positions (written
+            // by warp 0 before the last barrier) and writes those rows' block positions and
+            // E diagonal, none of which this pass touches; its own barrier then publishes both
+            // before the fused update reads the panel's rows.
+            if (pend >= brows) __syncthreads();
             r = r0 + np;
             Sprod = s_sprod;
         } else {
@@ -447,36 +463,70 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                 for (int t = 0; t < PIV_PB; ++t) pr[t] = s_prof[r0 + (t < bp ? t : 0)];
                 const int nwc = wne - r, ncol = nwc + pend;
                 const int nch = (ncol + 31) >> 5, nrg = (lim - pend + 7) >> 3;
-                for (int it = warp; it < nch * nrg; it += nw) {
-                    const int rg = it / nch, ch = it - rg * nch;
-                    const int ci = 32 * ch + lane;
-                    if (ci >= ncol) continue;
-                    const bool inw = ci < nwc;
-                    const int col = inw ? r + ci : ci - nwc;
-                    const uint32_t *ybase = inw ? W + col : E + col;
-                    const int ys = inw ? PIV_LDW : PIV_LDE;
-                    uint32_t y[PIV_PB];
+                // one entry: x <- A0 x + sum_t cf_t y_t
+                auto fused = [&](uint32_t *xp, const uint32_t (&cf)[PIV_PB], const uint32_t (&y)[PIV_PB]) {
+                    if (WIDE) {
+                        Acc acc = {(uint64_t)A0 * *xp, 0u};
 #pragma unroll
-                    for (int t = 0; t < PIV_PB; ++t) y[t] = ybase[pr[t] * ys];
-                    const int k0 = pend + 8 * rg, k1 = k0 + 8 < lim ? k0 + 8 : lim;
-                    uint32_t *xp = (inw ? W : E) + k0 * ys + col;
-                    for (int k = k0; k < k1; ++k, xp += ys) {
-                        const uint4 c0 = *(const uint4 *)&s_coef[k][0];
-                        const uint4 c1 = *(const uint4 *)&s_coef[k][4];
-                        const uint32_t cf[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-                        if (WIDE) {
-                            Acc acc = {(uint64_t)A0 * *xp, 0u};
+                        for (int t = 0; t < PIV_PB; ++t) acc_add(acc, (uint64_t)cf[t] * y[t]);
+                        *xp = acc_red(acc, M);
+                    } else {
+                        uint64_t sum = (uint64_t)A0 * *xp;
 #pragma unroll
-                            for (int t = 0; t < PIV_PB; ++t) acc_add(acc, (uint64_t)cf[t] * y[t]);
-                            *xp = acc_red(acc, M);
-                        } else {
-                            uint64_t sum = (uint64_t)A0 * *xp;
+                        for (int t = 0; t < PIV_PB; ++t) sum += (uint64_t)cf[t] * y[t];
+                        *xp = MONT ? redc_once(sum, M) : red64(sum, M);
+                    }
+                };
+                auto coefs = [&](const int k, uint32_t (&cf)[PIV_PB]) {
+                    const uint4 c0 = *(const uint4 *)&s_coef[k][0];
+                    const uint4 c1 = *(const uint4 *)&s_coef[k][4];
+                    cf[0] = c0.x; cf[1] = c0.y; cf[2] = c0.z; cf[3] = c0.w;
+                    cf[4] = c1.x; cf[5] = c1.y; cf[6] = c1.z; cf[7] = c1.w;
+                };
+                // Pipelined with the next panel when both take the fast path: warp 0 updates the
+                // next panel's 8 x 8 diagonal block itself and eliminates it at once (block_elim),
+                // while the other warps update everything else; the next panel then starts with
+                // its block done. A zero pivot there leaves the updated block in place for the
+                // stepwise path.
+                const bool pipe = fast && try_fast && brows - pend >= PIV_PB && r + PIV_PB <= wne;
+                if (pipe && warp == 0) {
+                    const int k = pend + (lane >> 2), c0 = r + 2 * (lane & 3);
+                    uint32_t cf[PIV_PB];
+                    coefs(k, cf);
 #pragma unroll
-                            for (int t = 0; t < PIV_PB; ++t) sum += (uint64_t)cf[t] * y[t];
-                            *xp = MONT ? redc_once(sum, M) : red64(sum, M);
+                    for (int e = 0; e < 2; ++e) {
+                        uint32_t y[PIV_PB];
+#pragma unroll
+                        for (int t = 0; t < PIV_PB; ++t) y[t] = W[pr[t] * PIV_LDW + c0 + e];
+                        fused(W + k * PIV_LDW + c0 + e, cf, y);
+                    }
+                    __syncwarp();
+                    block_elim(pend, r);
+                } else {
+                    const int w1 = pipe ? warp - 1 : warp, nw1 = pipe ? nw - 1 : nw;
+                    for (int it = w1; it < nch * nrg; it += nw1) {
+                        const int rg = it / nch, ch = it - rg * nch;
+                        const int ci = 32 * ch + lane;
+                        if (ci >= ncol) continue;
+                        const bool inw = ci < nwc;
+                        const int col = inw ? r + ci : ci - nwc;
+                        const uint32_t *ybase = inw ? W + col : E + col;
+                        const int ys = inw ? PIV_LDW : PIV_LDE;
+                        uint32_t y[PIV_PB];
+#pragma unroll
+                        for (int t = 0; t < PIV_PB; ++t) y[t] = ybase[pr[t] * ys];
+                        // the next panel's diagonal block is warp 0's when pipelined
+                        const int k0 = (pipe && rg == 0 && inw && ci < PIV_PB) ? pend + 8 : pend + 8 * rg;
+                        const int k1 = pend + 8 * rg + 8 < lim ? pend + 8 * rg + 8 : lim;
+                        uint32_t *xp = (inw ? W : E) + k0 * ys + col;
+                        for (int k = k0; k < k1; ++k, xp += ys) {
+                            uint32_t cf[PIV_PB];
+                            coefs(k, cf);
+                            fused(xp, cf, y);
                         }
                     }
                 }
+                pre_done = pipe;
             }
             __syncthreads();
         }
