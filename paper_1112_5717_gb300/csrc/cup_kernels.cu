@@ -46,6 +46,9 @@
 #define PIV_PB 8                    // panel rows of the blocked window elimination
 #endif
 #define PIV_PW 16                   // warps that eliminate a panel (all of them: 8 column chunks x 2 row parities)
+#ifndef PIV_QUIET
+#define PIV_QUIET 1                 // pipelined block update: leave warp 0's scheduler to warp 0
+#endif
 
 // One fraction-free update f x - m y, scaled by R^{-1} in the Montgomery
 // variant (odd p): the common factor only changes the tracked row scales.
@@ -184,44 +187,55 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         uint32_t fv = 0u;                     // lane t keeps the pivot of step t
         bool zero = false;
         // all eight steps unrolled; a zero pivot (the same value in every lane) is
-        // noted and the block's results are then discarded
+        // noted and the block's results are then discarded. Every lane computes its four
+        // updates and keeps them by selection: no divergent branch between the shuffles.
 #pragma unroll
         for (int t = 0; t < PIV_PB; ++t) {
             const int sf = 4 * t + (t >> 1), sm = 4 * k + (t >> 1), sy = 4 * t + jg;
-            const uint32_t fa = __shfl_sync(0xffffffffu, b0, sf), fb = __shfl_sync(0xffffffffu, b1, sf);
-            const uint32_t f = (t & 1) ? fb : fa;
+            const uint32_t f = __shfl_sync(0xffffffffu, (t & 1) ? b1 : b0, sf);
+            const uint32_t mk = __shfl_sync(0xffffffffu, (t & 1) ? b1 : b0, sm);
             zero |= f == 0u;
-            const uint32_t ma = __shfl_sync(0xffffffffu, b0, sm), mb = __shfl_sync(0xffffffffu, b1, sm);
             const uint32_t y0 = __shfl_sync(0xffffffffu, b0, sy), y1 = __shfl_sync(0xffffffffu, b1, sy);
             const uint32_t z0 = __shfl_sync(0xffffffffu, t0, sy), z1 = __shfl_sync(0xffffffffu, t1, sy);
-            const uint32_t mk = (t & 1) ? mb : ma;
-            if (lane == t) fv = f;
-            if (k > t) {
-                if (ja > t) b0 = ff<MONT>(f, b0, mk, y0, M);
-                if (jb > t) b1 = ff<MONT>(f, b1, mk, y1, M);
-                t0 = ff<MONT>(f, t0, mk, z0, M);
-                t1 = ff<MONT>(f, t1, mk, z1, M);
-            }
+            fv = (lane == t) ? f : fv;
+            const uint32_t n0 = ff<MONT>(f, b0, mk, y0, M), n1 = ff<MONT>(f, b1, mk, y1, M);
+            const uint32_t u0 = ff<MONT>(f, t0, mk, z0, M), u1 = ff<MONT>(f, t1, mk, z1, M);
+            const bool rk = k > t;
+            b0 = (rk && ja > t) ? n0 : b0;
+            b1 = (rk && jb > t) ? n1 : b1;
+            t0 = rk ? u0 : t0;
+            t1 = rk ? u1 : t1;
         }
         const bool ok = !zero;
         if (ok) {
             W[(bp0 + k) * PIV_LDW + br0 + ja] = b0;
             W[(bp0 + k) * PIV_LDW + br0 + jb] = b1;
-            s_T[k][ja] = t0;
-            s_T[k][jb] = t1;
+            // T R for odd p with narrow sums: the pass applying T then needs one
+            // Montgomery reduction per entry
+            s_T[k][ja] = (MONT && !WIDE) ? redc((uint64_t)t0 * M.r2, M) : t0;
+            s_T[k][jb] = (MONT && !WIDE) ? redc((uint64_t)t1 * M.r2, M) : t1;
             if (lane < PIV_PB) {
                 s_f[br0 + lane] = fv;
                 s_pos[br0 + lane] = (br0 + lane == 0 && ext0 >= 0) ? ext0 : br0 + lane;
                 s_prof[br0 + lane] = bp0 + lane;
             }
-            uint32_t S = Sprod;
+            // running scale before each step, S_t = Sprod * mu_0 ... mu_{t-1}, by an inclusive
+            // scan of the pivots over lanes 0 .. 7 (the identity is one, R in Montgomery form;
+            // every product of k factors carries R^{1-k} either way)
+            const uint32_t id = MONT ? redc((uint64_t)M.r2, M) : one;
+            uint32_t v = (lane < PIV_PB) ? fv : id;
 #pragma unroll
-            for (int t = 0; t < PIV_PB; ++t) {
-                const uint32_t ft = __shfl_sync(0xffffffffu, fv, t);
-                if (lane == 0) s_Sfwd[br0 + t] = S;
-                S = scale_mul<MONT>(S, ft, M);
+            for (int o = 1; o < PIV_PB; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                const uint32_t pv = scale_mul<MONT>(v, u, M);
+                v = (lane >= o) ? pv : v;
             }
-            if (lane == 0) s_sprod = S;
+            uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+            ex = (lane == 0) ? id : ex;
+            const uint32_t Sx = scale_mul<MONT>(Sprod, ex, M);     // S_lane (lane < 8)
+            const uint32_t Sall = scale_mul<MONT>(Sprod, __shfl_sync(0xffffffffu, v, PIV_PB - 1), M);
+            if (lane < PIV_PB) s_Sfwd[br0 + lane] = Sx;
+            if (lane == 0) s_sprod = Sall;
         }
         if (lane == 0) s_fast = ok ? 1 : 0;
     };
@@ -252,9 +266,11 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         }
         if (fast) {
             // window positions right of the block, then E columns [0, pend): thread per column,
-            // panel rows 1 .. np-1 as sums of T's entries times the rows' values before the panel
+            // panel rows 1 .. np-1 as sums of T's entries times the rows' values before the panel.
+            // Columns go to the last threads, whose warps the multiplier pass below leaves
+            // idle unless more than 4 (nw - 2) rows lie below the panel.
             const int nwc = wne - (r0 + np), ncol = nwc + pend;
-            for (int ci = tid; ci < ncol; ci += nt) {
+            for (int ci = nt - 1 - tid; ci < ncol; ci += nt) {
                 const bool inw = ci < nwc;
                 uint32_t *base = inw ? W + r0 + np + ci : E + (ci - nwc);
                 const int st = inw ? PIV_LDW : PIV_LDE;
@@ -264,13 +280,23 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 #pragma unroll
                 for (int kk = 1; kk < PIV_PB; ++kk) {
                     if (kk < np) {
-                        uint64_t s0 = 0, s1 = 0;      // at most four products below 2^62 in each
+                        if (MONT && !WIDE) {
+                            // s_T holds T R; at most eight products, each below p^2, sum
+                            // below p R (narrow sums mean p < 2^28.8), so one Montgomery
+                            // reduction gives sum T x
+                            uint64_t s0 = 0;
 #pragma unroll
-                        for (int j = 0; j <= kk; ++j) {
-                            if (j < 4) s0 += (uint64_t)s_T[kk][j] * x[j];
-                            else s1 += (uint64_t)s_T[kk][j] * x[j];
+                            for (int j = 0; j <= kk; ++j) s0 += (uint64_t)s_T[kk][j] * x[j];
+                            base[(p0 + kk) * st] = redc(s0, M);
+                        } else {
+                            uint64_t s0 = 0, s1 = 0;      // at most four products below 2^62 in each
+#pragma unroll
+                            for (int j = 0; j <= kk; ++j) {
+                                if (j < 4) s0 += (uint64_t)s_T[kk][j] * x[j];
+                                else s1 += (uint64_t)s_T[kk][j] * x[j];
+                            }
+                            base[(p0 + kk) * st] = addm(red64(s0, M), red64(s1, M), M);
                         }
-                        base[(p0 + kk) * st] = addm(red64(s0, M), red64(s1, M), M);
                     }
                 }
             }
@@ -378,7 +404,8 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 #pragma unroll
                 for (int o = 1; o < PIV_PB; o <<= 1) {
                     const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
-                    if (lane + o < bp) suf = redc((uint64_t)suf * u, M);
+                    const uint32_t ps = redc((uint64_t)suf * u, M);
+                    suf = (lane + o < bp) ? ps : suf;
                 }
                 const uint32_t oneR = redc((uint64_t)M.r2, M);
                 uint32_t ex = __shfl_down_sync(0xffffffffu, suf, 1);
@@ -397,7 +424,8 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 #pragma unroll
                 for (int o = 1; o < PIV_PB; o <<= 1) {
                     const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
-                    if (lane + o < bp) suf = mulm(suf, u, M);
+                    const uint32_t ps = mulm(suf, u, M);
+                    suf = (lane + o < bp) ? ps : suf;
                 }
                 h = __shfl_down_sync(0xffffffffu, suf, 1);
                 if (lane + 1 >= bp) h = one;
@@ -408,8 +436,8 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
             // the multipliers m_t by the recurrence restricted to the panel's pivot
             // positions (lane s holds position r0 + s; step t broadcasts lane t's value),
             // stored where the unblocked elimination leaves them, and the coefficients
-            // of the fused update (zero for t >= bp)
-            {
+            // of the fused update (zero for t >= bp); warps without such rows skip it
+            if (4 * warp < lim - pend) {
                 const int kr = 4 * warp + (lane >> 3), s = lane & 7;
                 const int k = pend + kr;
                 const bool vk = k < lim;
@@ -436,8 +464,10 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                 }
 #pragma unroll
                 for (int t = 0; t < PIV_PB - 1; ++t) {
+                    // computed by every lane and kept by selection (no branch between shuffles)
                     const uint32_t m = __shfl_sync(0xffffffffu, v, (lane & ~7) | t);
-                    if (t < bp && s > t && s < bp) v = ff<MONT>(fv[t], v, m, yv[t], M);
+                    const uint32_t nv = ff<MONT>(fv[t], v, m, yv[t], M);
+                    v = (t < bp && s > t && s < bp) ? nv : v;
                 }
                 if (vk) {
                     uint32_t cf = 0u;
@@ -502,8 +532,12 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
                     }
                     __syncwarp();
                     block_elim(pend, r);
-                } else {
-                    const int w1 = pipe ? warp - 1 : warp, nw1 = pipe ? nw - 1 : nw;
+                } else if (!(pipe && PIV_QUIET && (warp & 3) == 0)) {
+                    // With PIV_QUIET the warps that share warp 0's scheduler (warp % 4 == 0
+                    // on this GPU) stay out of a pipelined update, so that the block
+                    // elimination on warp 0's dependency chain issues without contention.
+                    const int w1 = !pipe ? warp : PIV_QUIET ? warp - (warp >> 2) - 1 : warp - 1;
+                    const int nw1 = !pipe ? nw : PIV_QUIET ? nw - (nw >> 2) : nw - 1;
                     for (int it = w1; it < nch * nrg; it += nw1) {
                         const int rg = it / nch, ch = it - rg * nch;
                         const int ci = 32 * ch + lane;
@@ -1127,9 +1161,12 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
         });
         if (e != cudaSuccess) return e;
     }
-    // the block update sums PIV_PB + 1 products below p^2 in 64 bits when that cannot wrap
+    // The block update sums PIV_PB + 1 products below p^2 in 64 bits when that cannot wrap;
+    // for odd p that sum is reduced by one Montgomery step, which needs it below p 2^32
+    // (p < 2^28.8). Larger p take the wide accumulators.
     const uint64_t pm1 = M.p - 1u;
-    const bool wide = pm1 * pm1 > ~0ull / (uint64_t)(PIV_PB + 1);
+    const bool wide = pm1 * pm1 > ~0ull / (uint64_t)(PIV_PB + 1) ||
+                      ((M.p & 1u) && (unsigned __int128)(PIV_PB + 1) * pm1 * pm1 >= ((unsigned __int128)M.p << 32));
     if (M.p & 1u) {
         if (wide)
             return launch_pdl(k_slab_pivots<true, true>, 1, PIV_THREADS, smem, st, A, lda, a, brows, col0, n, wn,

@@ -102,6 +102,8 @@ def _factor_case(cup, A, p, **opts):
     h.close()
 
 
+P_NARROW_TOP = inputs.primes_below((1 << 32) // 9 + 1, 1)[0]
+
 FACTOR_CASES = {
     "dense_plain_512": lambda: (inputs.dense_plain(), inputs.P_16),
     "dense_full_300": lambda: (inputs.dense_full(n=300), inputs.P_16),
@@ -112,6 +114,10 @@ FACTOR_CASES = {
     "one_row": lambda: (inputs.dense_full(m=1, n=77, p=251), 251),
     "one_col": lambda: (inputs.dense_full(m=77, n=1, p=251), 251),
     "p31": lambda: (inputs.dense_full(n=200, p=2147483647), 2147483647),
+    # the largest odd p whose nine-product block-update sums still fit one Montgomery
+    # reduction (9 (p-1)^2 < p 2^32), and a p above that bound (wide sums)
+    "p_narrow_top": lambda: (inputs.dense_full(n=300, p=P_NARROW_TOP), P_NARROW_TOP),
+    "p30": lambda: (inputs.dense_full(n=300, p=1073741789), 1073741789),
 }
 
 
@@ -153,7 +159,7 @@ def test_det(cuda_lib, n, p):
 
 
 @pytest.mark.parametrize("name", ["dense_plain_512", "rank_def_700x256", "wide_90x500_p2",
-                                  "tall_500x90_p3", "p31", "dense_full_300"])
+                                  "tall_500x90_p3", "p31", "dense_full_300", "p_narrow_top", "p30"])
 @pytest.mark.parametrize("tc_min_k", [1, 64])
 def test_factor_tensor_engine(cuda_lib, name, tc_min_k):
     A, p = FACTOR_CASES[name]()
