@@ -69,8 +69,12 @@ enum {
     CUP_OPT_SCHEDULE = 6,      /* cup_factor schedule: 1 (default) device-resident, replayed as a CUDA
                                   graph when a call repeats; 2 device-resident without graphs; 0 host-driven
                                   (reads each block's rank back before launching the next) */
-    CUP_OPT_INT_PATH = 7       /* images of cup_int_det / cup_int_rank: 0 (default) by a cost model,
+    CUP_OPT_INT_PATH = 7,      /* images of cup_int_det / cup_int_rank: 0 (default) by a cost model,
                                   1 the batched launch (min(m, n) <= 2048), 2 one full-device CUP per prime */
+    CUP_OPT_SHORT_K = 8        /* tensor-engine Schur updates with K at most this (0..128, default 128),
+                                  p < 2^24 and at most 2^21 entries of C run as one launch of
+                                  mma.sync digit products formed in shared memory instead of a digit
+                                  split plus a tcgen05 launch; 0 sends every update to tcgen05 */
 };
 
 /* Counters of the work a handle has enqueued since the last cup_reset_stats.
@@ -89,6 +93,9 @@ typedef struct {
     double cc_field_flops;
     double tc_alg_bytes;       /* algorithmic HBM bytes of the tcgen05 launches: limb planes read
                                   (2 L (M + N) K) plus C read and written (8 M N), summed */
+    int64_t sk_launches;       /* short-K tensor updates (CUP_OPT_SHORT_K) */
+    double sk_ms;              /* their summed device time */
+    double sk_field_flops;     /* 2 M N K over those launches */
 } cup_stats;
 
 /* Create a handle bound to CUDA device `device` (the device is made current

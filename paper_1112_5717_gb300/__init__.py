@@ -25,6 +25,7 @@ ENGINE_PLAIN = 0
 ENGINE_TENSOR = 1
 OPT_ENGINE, OPT_LEAF_ROWS, OPT_WINDOW, OPT_TC_MIN_K, OPT_VALIDATE, OPT_PROFILE, OPT_SCHEDULE = 0, 1, 2, 3, 4, 5, 6
 OPT_INT_PATH = 7
+OPT_SHORT_K = 8
 
 
 class Stats(ctypes.Structure):
@@ -33,7 +34,9 @@ class Stats(ctypes.Structure):
                 ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
                 ("tc_limb_flops", ctypes.c_double), ("tc_field_flops", ctypes.c_double),
                 ("cc_launches", ctypes.c_int64), ("cc_ms", ctypes.c_double),
-                ("cc_field_flops", ctypes.c_double), ("tc_alg_bytes", ctypes.c_double)]
+                ("cc_field_flops", ctypes.c_double), ("tc_alg_bytes", ctypes.c_double),
+                ("sk_launches", ctypes.c_int64), ("sk_ms", ctypes.c_double),
+                ("sk_field_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -198,7 +201,7 @@ class Handle:
             self.set_option(OPT_ENGINE, engine)
         names = {"leaf_rows": OPT_LEAF_ROWS, "window": OPT_WINDOW, "tc_min_k": OPT_TC_MIN_K,
                  "validate": OPT_VALIDATE, "profile": OPT_PROFILE, "schedule": OPT_SCHEDULE,
-                 "int_path": OPT_INT_PATH}
+                 "int_path": OPT_INT_PATH, "short_k": OPT_SHORT_K}
         for k, v in opts.items():
             self.set_option(names[k], int(v))
 

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcup_gb300.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["cup_kernels.cu", "cup_tc.cu", "cup_tri.cu", "cup_batched.cu", "cup_int.cu", "cup_api.cu"]
+SOURCES = ["cup_kernels.cu", "cup_tc.cu", "cup_short.cu", "cup_tri.cu", "cup_batched.cu", "cup_int.cu",
+           "cup_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

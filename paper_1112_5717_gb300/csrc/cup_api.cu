@@ -32,6 +32,7 @@ struct cup_handle {
     int leaf_rows = 64;
     int window = 96;
     int64_t tc_min_k = 64;
+    int64_t short_k = SHORT_K_MAX;  // largest K of the one-launch short-K tensor update (0: never)
     bool user_set[3] = {false, false, false};   // leaf_rows, window, tc_min_k set by cup_set_option
     struct TuneRule {
         int64_t limbs = -1, tall = -1, min_lo = 0, min_hi = INT64_MAX;
@@ -83,13 +84,14 @@ struct cup_handle {
         const uint8_t *dev8 = nullptr;    // one-byte input (or its staging copy) widened by the graph
         int64_t ld8 = 0;
         int esize = 4;
+        int64_t short_k = 0;
     };
     int64_t gen = 0;                   // bumped whenever a buffer a graph may reference moves
     std::vector<GraphEntry> graphs;
     cup_stats stats = {};
     struct Timed { cudaEvent_t e0, e1; double limb_flops, field_flops; int cls; };
     std::vector<Timed> graph_timed;    // event pairs baked into captured graphs
-    double cls_ms[8] = {0};        // per kernel class, profile level >= 2
+    double cls_ms[9] = {0};        // per kernel class, profile level >= 2 (8: short-K updates)
     std::vector<Timed> pending;    // recorded intervals not yet read
     std::vector<cudaEvent_t> evpool;
     char err[256] = {0};
@@ -182,6 +184,7 @@ void flush_timings(cup_handle *h)
         if (t.e0 && t.e1 && cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
             if (t.cls == 0) h->stats.tc_ms += ms;
             else if (t.cls == 1) h->stats.cc_ms += ms;
+            else if (t.cls == 8) h->stats.sk_ms += ms;
             h->cls_ms[t.cls] += ms;
         }
         if (t.e0) h->evpool.push_back(t.e0);
@@ -199,7 +202,8 @@ cup_status sync_stream(cup_handle *h, cudaStream_t st)
 }
 
 // Interval of one kernel class (profile level >= 2): classes 2 = base-case
-// pivots, 3 = base-case finish, 4 = TRSM leaf, 5 = transpositions, 6 = limb split.
+// pivots, 3 = base-case finish, 4 = TRSM leaf, 5 = transpositions, 6 = a whole
+// tcgen05 update (limb split and product).
 struct ClassTimer {
     cup_handle *h;
     cudaStream_t st;
@@ -285,6 +289,20 @@ cup_status mm_sub(cup_handle *h, uint32_t *C, int64_t ldc, const uint32_t *A, in
                   int engine, cudaStream_t st, int add = 0)
 {
     if (M <= 0 || N <= 0 || K <= 0) return CUP_OK;
+    if (engine == CUP_ENGINE_TENSOR && K >= h->tc_min_k && gemm_short_ok(Mp.p, M, N, K, h->short_k)) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->profile) { e0 = take_event(h); e1 = take_event(h); if (e0) cudaEventRecord(e0, st); }
+        GemmDesc d{A, lda, dconst(0), dconst(0), B, ldb, dconst(0), dconst(0), C, ldc, dconst(0), dconst(0),
+                   M, dconst(N), dconst(K), add};
+        CU(launch_gemm_short_desc(d, Mp, st));
+        if (e1) cudaEventRecord(e1, st);
+        const double f = 2.0 * (double)M * (double)N * (double)K;
+        h->stats.launches += 1;
+        h->stats.sk_launches += 1;
+        h->stats.sk_field_flops += f;
+        if (h->profile) h->pending.push_back({e0, e1, 0.0, f, 8});
+        return CUP_OK;
+    }
     if (engine == CUP_ENGINE_TENSOR && K >= h->tc_min_k) {
         CK(ensure_base(h));
         CK(ensure_ws(h, tc_workspace_bytes(Mp.p, M, N, K)));
@@ -595,9 +613,15 @@ cup_status dev_gemm(DevCtx &c, const GemmDesc &g)
     cup_handle *h = c.h;
     if (g.M <= 0 || g.N.hi <= 0 || g.K.hi <= 0) return CUP_OK;
     const bool tc = h->engine == CUP_ENGINE_TENSOR && g.K.hi >= h->tc_min_k;
+    const bool sk = tc && gemm_short_ok(c.M.p, g.M, g.N.hi, g.K.hi, h->short_k);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profile) { e0 = take_event(h); e1 = take_event(h); }
-    if (tc) {
+    if (sk) {
+        if (e0) cudaEventRecord(e0, c.st);
+        CU(launch_gemm_short_desc(g, c.M, c.st));
+        if (e1) cudaEventRecord(e1, c.st);
+        h->stats.launches += 1;
+    } else if (tc) {
         ClassTimer tm(h, c.st, 6);
         CU(launch_gemm_tc_desc(g, c.M, h->d_ws, h->d_err, c.st, e0, e1));
         h->stats.launches += 3;
@@ -607,9 +631,9 @@ cup_status dev_gemm(DevCtx &c, const GemmDesc &g)
         if (e1) cudaEventRecord(e1, c.st);
         h->stats.launches += 1;
     }
-    if (h->profile) h->pending.push_back({e0, e1, 0.0, 0.0, tc ? 0 : 1});
+    if (h->profile) h->pending.push_back({e0, e1, 0.0, 0.0, sk ? 8 : tc ? 0 : 1});
     GemmDesc rec = g;
-    rec.add = tc ? 1 : 0;               // reused as the engine tag in the record
+    rec.add = sk ? 2 : tc ? 1 : 0;      // reused as the engine tag in the record
     c.gemms->push_back(rec);
     return CUP_OK;
 }
@@ -649,7 +673,8 @@ cup_status dev_trsm(DevCtx &c, const int64_t *col0p, const int64_t *midp, int64_
     GemmDesc g{c.A, c.lda, dconst(a2), dvar(j0, col0p, 1, nullptr, 0, 0, c.n),
                c.A, c.lda, dvar(j0, col0p, 1, nullptr, 0, 0, c.n), dvar(j0 + k, col0p, 1, nullptr, 0, 0, c.n),
                c.A, c.lda, dconst(a2), dvar(j0 + k, col0p, 1, nullptr, 0, 0, c.n),
-               m2, dvar(-j0 - k, midp, 1, col0p, -1, 0, len - k), dvar(-j0, midp, 1, col0p, -1, 0, k), 0};
+               m2, dvar(-j0 - k, midp, 1, col0p, -1, 0, len - k), dvar(-j0, midp, 1, col0p, -1, 0, k), 0,
+               1};   // the launch before is the TRSM leaf that wrote A (G's first columns) only
     CK(dev_gemm(c, g));
     CK(dev_trsm(c, col0p, midp, a2, m2, j0 + k, len - k));
     return CUP_OK;
@@ -692,7 +717,8 @@ cup_status dev_rec(DevCtx &c, int64_t a, int64_t mrows)
     GemmDesc g{c.A, c.lda, dconst(a2), dvar(0, col0p, 1, nullptr, 0, 0, c.n),
                c.A, c.lda, dvar(0, col0p, 1, nullptr, 0, 0, c.n), dvar(0, midp, 1, nullptr, 0, 0, c.n),
                c.A, c.lda, dconst(a2), dvar(0, midp, 1, nullptr, 0, 0, c.n),
-               m2, dvar(c.n, midp, -1, nullptr, 0, 0, c.n), dvar(0, midp, 1, col0p, -1, 0, kmax), 0};
+               m2, dvar(c.n, midp, -1, nullptr, 0, 0, c.n), dvar(0, midp, 1, col0p, -1, 0, kmax), 0,
+               1};   // the launch before is the TRSM leaf that wrote A (G) only
     CK(dev_gemm(c, g));
     CK(dev_rec(c, a2, m2));
     const int L1 = c.nleaf;
@@ -823,7 +849,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
         if (e.A == A && e.m == m && e.n == n && e.lda == lda && e.p == p && e.prof == d_profile && e.hA == hA &&
             e.ldh == ldh && e.dev8 == src.dev8 && e.ld8 == src.ld8 && e.esize == src.esize &&
             e.ipiv == d_ipiv && e.st == st && e.leaf_rows == h->leaf_rows && e.window == h->window &&
-            e.engine == h->engine && e.tc_min_k == h->tc_min_k)
+            e.engine == h->engine && e.tc_min_k == h->tc_min_k && e.short_k == h->short_k)
             ge = &e;
     if (ge && ge->gen != h->gen) {
         if (ge->exec) cudaGraphExecDestroy(ge->exec);
@@ -926,7 +952,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
             // remember the call; the next identical one is captured and replayed
             cup_handle::GraphEntry e{A, m, n, lda, p, d_profile, d_ipiv, st, h->leaf_rows, h->window, h->engine,
                                      h->tc_min_k, h->gen, nullptr, 0, false, {}, {}, hA, ldh, src.dev8, src.ld8,
-                                     src.esize};
+                                     src.esize, h->short_k};
             if (h->graphs.size() > 16) {
                 if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
                 h->graphs.erase(h->graphs.begin());
@@ -943,6 +969,7 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
             if (t.e0 && t.e1 && cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
                 if (t.cls == 0) h->stats.tc_ms += ms;
                 else if (t.cls == 1) h->stats.cc_ms += ms;
+                else if (t.cls == 8) h->stats.sk_ms += ms;
                 h->cls_ms[t.cls] += ms;
             } else {
                 cudaGetLastError();          // an interval the graph could not time: leave it out
@@ -958,7 +985,10 @@ cup_status factor_device(cup_handle *h, uint32_t *A, int64_t m, int64_t n, int64
             const double gn = (double)host_eval(g.N, h->d_rank_at, h->h_rank),
                          gk = (double)host_eval(g.K, h->d_rank_at, h->h_rank);
             const double f = 2.0 * (double)g.M * gn * gk;
-            if (g.add) {
+            if (g.add == 2) {
+                h->stats.sk_launches += 1;
+                h->stats.sk_field_flops += f;
+            } else if (g.add) {
                 h->stats.tc_launches += 1;
                 h->stats.tc_field_flops += f;
                 h->stats.tc_limb_flops += f * L * L;
@@ -1189,6 +1219,10 @@ cup_status cup_set_option(cup_handle *h, int option, int64_t value)
     case CUP_OPT_INT_PATH:
         if (value < 0 || value > 2) return CUP_ERR_ARG;
         h->int_path = (int)value;
+        return CUP_OK;
+    case CUP_OPT_SHORT_K:
+        if (value < 0 || value > SHORT_K_MAX) return CUP_ERR_ARG;
+        h->short_k = value;
         return CUP_OK;
     default:
         return CUP_ERR_ARG;

@@ -62,6 +62,33 @@ __device__ __forceinline__ void pdl_enter()
 // still pass pdl_enter before it exits, which keeps the chain ordered.
 #endif
 
+#ifdef __CUDACC__
+#include <cuda_bf16.h>
+// Centred base-256 digits of a residue: x = sum_l d_l 256^l (mod p), |d_l| <= 128,
+// exact in bf16.
+template <int L>
+__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, __nv_bfloat16 (&d)[L])
+{
+    int32_t v = (x > (p >> 1)) ? (int32_t)(x - p) : (int32_t)x;
+#pragma unroll
+    for (int l = 0; l < L - 1; ++l) {
+        const int32_t dl = ((v + 128) & 255) - 128;
+        d[l] = __int2bfloat16_rn(dl);
+        v = (v - dl) >> 8;
+    }
+    d[L - 1] = __int2bfloat16_rn(v);
+}
+
+// D += A B for one 16 x 8 tile: A 16 x 16 (row), B 16 x 8 (col), bf16 in, fp32 accumulate.
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+#endif
+
 template <typename... KArgs, typename... Args>
 static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                      Args... args)
@@ -128,6 +155,10 @@ struct GemmDesc {
     int64_t M;
     Dyn N, K;
     int add;
+    // 1: B, C and the extents were written at least two launches back on the stream (the
+    // launch just before writes only A), so a kernel launched with launch_pdl may read
+    // them before waiting for its predecessor
+    int pre = 0;
 };
 
 // A right-side triangular operation B <- B T^{-1} (or B T) with B rows x n and
@@ -198,6 +229,14 @@ cudaError_t launch_det_reduce(const uint32_t *A, int64_t lda, int64_t n, const i
 
 // Tensor-core Schur update (cup_tc.cu).
 int tc_limbs(uint32_t p);
+
+// One-launch short-K tensor update (cup_short.cu): mma.sync on digits made in
+// shared memory, for K <= SHORT_K_MAX, p < 2^24 and at most SHORT_MAX_OUTPUTS
+// entries of C (beyond that the tcgen05 path's throughput wins).
+#define SHORT_K_MAX 128
+#define SHORT_MAX_OUTPUTS (1ll << 21)
+bool gemm_short_ok(uint32_t p, int64_t M, int64_t Nhi, int64_t Khi, int64_t kmax);
+cudaError_t launch_gemm_short_desc(const GemmDesc &d, ModP M, cudaStream_t st);
 size_t tc_workspace_bytes(uint32_t p, int64_t M, int64_t N, int64_t K);
 cudaError_t launch_gemm_tc_desc(const GemmDesc &d, ModP Mp, void *ws, int *err, cudaStream_t st,
                                 cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);

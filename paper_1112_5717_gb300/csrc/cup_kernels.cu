@@ -664,30 +664,6 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 // matrix) and C in the slab rows. Rows taken as dependent by a speculating
 // pivot kernel are checked here: their residual x - C u must vanish.
 // ---------------------------------------------------------------------------
-// Centred base-256 digits of a residue: x = sum_l d_l 256^l (mod p), |d_l| <= 128,
-// exact in bf16.
-template <int L>
-__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, __nv_bfloat16 (&d)[L])
-{
-    int32_t v = (x > (p >> 1)) ? (int32_t)(x - p) : (int32_t)x;
-#pragma unroll
-    for (int l = 0; l < L - 1; ++l) {
-        const int32_t dl = ((v + 128) & 255) - 128;
-        d[l] = __int2bfloat16_rn(dl);
-        v = (v - dl) >> 8;
-    }
-    d[L - 1] = __int2bfloat16_rn(v);
-}
-
-// D += A B for one 16 x 8 tile: A 16 x 16 (row), B 16 x 8 (col), bf16 in, fp32 accumulate.
-__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 #define FIN_LD 72   // bf16 row stride of the digit planes (144 bytes: conflict-free fragment loads)
 
 // MODE 0 / 1: U = Linv X by 64-bit CUDA-core products (1: wide sums); MODE 2 + l:
