@@ -570,7 +570,9 @@ def run_ours(args):
         src = "measured burst bf16 (MEASURED_PEAKS.json)"
         if peak is None:
             peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16"
-        traffic, tnote = captured_traffic(wkey(args, opts, engine == cup.ENGINE_TENSOR))
+        tsteps = args.roofline_steps if args.profile == 0 else args.steps
+        traffic, tnote = captured_traffic(wkey(args, opts, engine == cup.ENGINE_TENSOR),
+                                          rst["tc_launches"] / max(tsteps, 1))
         result["roofline"] = {"bound": "tensor", "kernel": "k_limb_gemm", "achieved": achieved, "peak": peak,
                               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                               "traffic_unit": "bytes per launch", "traffic_source": tnote,
@@ -673,9 +675,10 @@ def wkey(args, opts, tensor: bool) -> str:
     return f"{args.workload}:{args.n or 'default'}:{args.op}"
 
 
-def captured_traffic(key: str):
+def captured_traffic(key: str, launches_per_step=None):
     """(bytes per launch, source) from the traffic file when it holds a capture of this
-    configuration taken with the current tensor-kernel source; else (None, why)."""
+    configuration taken with the current tensor-kernel source and the same number of
+    tensor-kernel launches per step; else (None, why)."""
     import hashlib
     try:
         data = json.load(open(TRAFFIC_FILE))
@@ -687,6 +690,8 @@ def captured_traffic(key: str):
     sha = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
     if rec.get("source_sha256") != sha:
         return None, "stale: the tensor kernel changed since its ncu capture"
+    if launches_per_step and rec.get("launches") and round(launches_per_step) != rec["launches"]:
+        return None, "stale: the step's tensor-kernel launches changed since its ncu capture"
     return rec["bytes_per_launch"], rec.get("capture", "ncu")
 
 
