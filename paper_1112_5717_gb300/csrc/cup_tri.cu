@@ -295,7 +295,9 @@ k_trsm_ruu128(const TriDesc d, ModP M)
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int base = threadIdx.x; base < n * RUU_MAX; base += 8 * blockDim.x) {
+    // MODE 3 reads only the strictly upper part of rows and columns below n and tolerates
+    // anything elsewhere (see the solve), so it skips this pass
+    for (int base = threadIdx.x; MODE != 3 && base < n * RUU_MAX; base += 8 * blockDim.x) {
         // eight independent entries per pass (all read before any is written)
         uint32_t v[8];
 #pragma unroll
@@ -312,34 +314,70 @@ k_trsm_ruu128(const TriDesc d, ModP M)
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t c24 = (uint32_t)((1u << 24) % M.p), mu32 = (uint32_t)(0xffffffffu / M.p);
-    // MODE 3: V_b = inverse of the b-th 32 x 32 diagonal block (unit upper), by warp b;
-    // lane j keeps column j in registers and runs the back substitution
-    // V[k][j] = -sum_{l > k} U[k][l] V[l][j] from the bottom row up (rows past n stay
-    // identity rows)
+    // MODE 3: V_b = inverse of the b-th 32 x 32 diagonal block (unit upper), in two steps.
+    // (1) Warp w inverts the 16 x 16 diagonal block w (lane j keeps column j in registers
+    // and runs the back substitution V[k][j] = -sum_{l > k} U[k][l] V[l][j] from the
+    // bottom row up; rows at or past n stay identity rows), writing it into its quadrant
+    // of V_b. (2) With A, D the two 16 x 16 diagonal blocks of block b and B the block
+    // between them, V_b's upper-right quadrant is -A^{-1} (B D^{-1}) (two 16 x 16 x 16
+    // products over all threads) and its lower-left quadrant is zero. Entries of U outside
+    // the strictly upper n x n part are never combined with a nonzero factor in a valid
+    // position, so the unmasked triangle is safe; every sum here has at most 16 products
+    // below 2^32.
     uint32_t *const sV = sU + RUU_MAX * RUU_LDS;
     if (MODE == 3) {
+        const int nblk = (n + 31) >> 5;
         const int wv = threadIdx.x >> 5;
-        if (wv < 4 && 32 * wv < n) {
-            const int b0 = 32 * wv;
-            const int nbr = n - b0 < 32 ? n - b0 : 32;
-            uint32_t v[32];
+        if (wv < 2 * nblk) {
+            const int b = wv >> 1, h = wv & 1, o = 16 * wv, j = lane & 15;
+            const int nsb = n - o;                        // valid rows of this sub-block (may be <= 0)
+            uint32_t v[16];
 #pragma unroll
-            for (int l = 0; l < 32; ++l) v[l] = (l == lane) ? 1u : 0u;
+            for (int l = 0; l < 16; ++l) v[l] = (l == j) ? 1u : 0u;
+            // no branch in the chain: every step's loads are unconditional (rows past n
+            // lie inside sU) and its result is kept by selection
 #pragma unroll
-            for (int k = 30; k >= 0; --k) {
-                if (k < nbr) {
-                    const uint32_t *uk = sU + (b0 + k) * RUU_LDS + b0;
-                    // four partial sums: the chain of 64-bit adds is a quarter as long
-                    uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
+            for (int k = 14; k >= 0; --k) {
+                const uint32_t *uk = sU + (o + k) * RUU_LDS + o;
+                uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-                    for (int l = k + 1; l < 32; ++l) s4[l & 3] += (uint64_t)uk[l] * v[l];
-                    const uint32_t r = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
-                    if (k < lane) v[k] = r ? M.p - r : 0u;
+                for (int l = k + 1; l < 16; ++l) s4[l & 3] += (uint64_t)uk[l] * v[l];
+                const uint32_t r = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
+                v[k] = (k < nsb && k < j) ? (r ? M.p - r : 0u) : v[k];
+            }
+            uint32_t *V = sV + b * 32 * TRI_VLD + 16 * h * (TRI_VLD + 1);
+            if (lane < 16) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) V[k * TRI_VLD + j] = v[k];
+            } else {
+                // the lower-left quadrant of V_b is zero (warp 2b writes it)
+                if (h == 0) {
+                    uint32_t *Z = sV + b * 32 * TRI_VLD + 16 * TRI_VLD;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) Z[k * TRI_VLD + j] = 0u;
                 }
             }
-            uint32_t *V = sV + wv * 32 * TRI_VLD;
+        }
+        __syncthreads();
+        uint32_t *const sY = sV + 4 * 32 * TRI_VLD;       // 4 x 16 x 17: B D^{-1} per block
+        for (int idx = threadIdx.x; idx < nblk * 256; idx += blockDim.x) {
+            const int b = idx >> 8, l = (idx >> 4) & 15, jj = idx & 15;
+            const uint32_t *Bl = sU + (32 * b + l) * RUU_LDS + 32 * b + 16;
+            const uint32_t *D = sV + b * 32 * TRI_VLD + 16 * TRI_VLD + 16 + jj;
+            uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-            for (int k = 0; k < 32; ++k) V[k * TRI_VLD + lane] = v[k];
+            for (int m2 = 0; m2 < 16; ++m2) s4[m2 & 3] += (uint64_t)Bl[m2] * D[m2 * TRI_VLD];
+            sY[(b * 16 + l) * 17 + jj] = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nblk * 256; idx += blockDim.x) {
+            const int b = idx >> 8, k = (idx >> 4) & 15, jj = idx & 15;
+            const uint32_t *Ak = sV + b * 32 * TRI_VLD + k * TRI_VLD;
+            uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+            for (int l = 0; l < 16; ++l) s4[l & 3] += (uint64_t)Ak[l] * sY[(b * 16 + l) * 17 + jj];
+            const uint32_t r = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
+            sV[b * 32 * TRI_VLD + k * TRI_VLD + 16 + jj] = r ? M.p - r : 0u;
         }
         __syncthreads();
     }
@@ -366,7 +404,9 @@ k_trsm_ruu128(const TriDesc d, ModP M)
                 uint64_t s4[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
                 for (int k = 0; k < 32; ++k) s4[k & 3] += (uint64_t)__shfl_sync(0xffffffffu, y, k) * V[k * TRI_VLD];
-                const uint32_t x = red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32);
+                // lanes at or past n hold no value (their sums may mix unmasked entries): zero
+                const uint32_t x = (32 * b + lane < n) ? red39((s4[0] + s4[1]) + (s4[2] + s4[3]), M.p, c24, mu32)
+                                                       : 0u;
                 xo[b] = x;
                 if (b < 3 && 32 * (b + 1) < n) {
                     const uint32_t nx = x ? M.p - x : 0u;
@@ -433,7 +473,7 @@ cudaError_t launch_trsm_ruu_desc(const TriDesc &d, ModP M, cudaStream_t st)
     if (d.rows <= 0 || d.n.hi <= 0) return cudaSuccess;
     if (d.n.hi > RUU_MAX) return cudaErrorInvalidValue;
     static PerDeviceOnce attr;
-    const size_t smem = ((size_t)RUU_MAX * RUU_LDS + 4 * 32 * TRI_VLD) * sizeof(uint32_t);
+    const size_t smem = ((size_t)RUU_MAX * RUU_LDS + 4 * 32 * TRI_VLD + 4 * 16 * 17) * sizeof(uint32_t);
     {
         const cudaError_t e = once_per_device(attr, [&] {
             cudaError_t e2 = cudaFuncSetAttribute(k_trsm_ruu128<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
