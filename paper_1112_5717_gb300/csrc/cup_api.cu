@@ -529,7 +529,7 @@ cup_status cup_rec(Ctx &c, int64_t a, int64_t mrows, int64_t col0, int64_t *r_ou
         CU(cudaMemcpyAsync(h->h_pinned, h->d_slab, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
         {
         ClassTimer tm(h, c.st, 3);
-        CU(launch_slab_finish(c.A, c.lda, a, dconst(col0), c.n, c.M, h->d_slab, nullptr, c.st,
+        CU(launch_slab_finish(c.A, c.lda, a, (int)mrows, dconst(col0), c.n, c.M, h->d_slab, nullptr, c.st,
                               h->engine == CUP_ENGINE_TENSOR));
         }
         h->stats.launches += 2;
@@ -695,7 +695,7 @@ cup_status dev_rec(DevCtx &c, int64_t a, int64_t mrows)
         }
         {
             ClassTimer tm(h, c.st, 3);
-            CU(launch_slab_finish(c.A, c.lda, a, col0, c.n, c.M, h->d_slab, h->d_err, c.st,
+            CU(launch_slab_finish(c.A, c.lda, a, (int)mrows, col0, c.n, c.M, h->d_slab, h->d_err, c.st,
                                   h->engine == CUP_ENGINE_TENSOR));
         }
         h->stats.launches += 2;

@@ -42,6 +42,17 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// Close the group of this thread's copies issued so far; cp_async_wait_prior<N>() then
+// waits until at most the N most recent groups are still in flight.
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_prior()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 #endif
 
 #ifdef __CUDACC__
@@ -213,7 +224,7 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
                                int64_t *rank_next, cudaStream_t st);
 // tensor: U = L^{-1} X by bf16 digit products on mma.sync for p < 2^24 (the tensor
 // engine); otherwise, and for the plain engine, by 64-bit CUDA-core products.
-cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, int64_t n, ModP M,
+cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int brows, Dyn col0, int64_t n, ModP M,
                                const SlabScratch *S, int *err, cudaStream_t st, bool tensor);
 cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st);
 cudaError_t launch_laswp(uint32_t *A, int64_t lda, Dyn row0, Dyn nrows, const int2 *pairs, const int *count,

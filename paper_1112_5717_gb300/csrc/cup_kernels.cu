@@ -671,25 +671,39 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
 // 64 * l * 2^14 < 2^24), recombined in 64 bits.
 template <int MODE>
 __global__ void __launch_bounds__(256)
-k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d, int64_t n, ModP M,
+k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const Dyn col0d, int64_t n, ModP M,
               SlabScratch *__restrict__ S, int *__restrict__ err, uint64_t off)
 {
-    pdl_enter();
     constexpr bool WIDE = MODE == 1;
     constexpr int TCL = MODE >= 2 ? MODE - 1 : 0;
     constexpr int TL = TCL > 0 ? TCL : 1;            // array extent for the digit code
+    // The launch just before this one is the slab's pivot kernel, which writes the
+    // scratch S but not A, and col0 comes from the leaf before: the slab rows' values
+    // in this tile's columns (the pivot rows' original values, except at displaced
+    // positions, which S->Dorig keeps) are copied in before the dependency wait.
     const int64_t col0 = col0d.eval();
     const int64_t w = n - col0;
+    const int64_t q0 = (int64_t)blockIdx.x * CUP_QT;
+    if (q0 >= w) {
+        pdl_enter();
+        return;
+    }
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
+    extern __shared__ __align__(16) uint8_t fdyn[];
+    uint32_t (*sTile)[CUP_QT] = (uint32_t (*)[CUP_QT])(fdyn + (TCL > 0 ? 2 * TCL * CUP_BMAX * FIN_LD * 2 : 0));
+    for (int idx = tid; idx < brows * CUP_QT; idx += nt) {
+        const int i = idx >> 6, qq = idx & (CUP_QT - 1);
+        if (qq < nq) cp_async4(&sTile[i][qq], A + (a + i) * lda + col0 + q0 + qq);
+    }
+    cp_async_commit();
+    pdl_enter();
     __shared__ uint32_t sL[CUP_BMAX][CUP_BMAX + 1];
     __shared__ uint32_t sX[CUP_BMAX][CUP_QT + 1];
     __shared__ uint32_t sPinv[CUP_BMAX];
     __shared__ int sOrig[CUP_QT], sSlot[CUP_QT], sProf[CUP_BMAX];
 
     const int rs = S->r_s, stop = S->i_stop, wne = S->wne;
-    const int64_t q0 = (int64_t)blockIdx.x * CUP_QT;
-    if (q0 >= w) return;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
     const int ext_pos = S->ext_pos, ext_slot = S->ext_slot;
     if (TCL > 0 && q0 == 0) {
         // the first tile also writes the slab's C values (positions < r_s <= CUP_QT);
@@ -700,6 +714,7 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
             if (i < stop && t < rs) cp_async4(&sL[i][t], &S->Cn[i][t]);
         }
     }
+    cp_async_commit();
 
     for (int t = tid; t < rs; t += nt) { sProf[t] = S->prof[t]; sPinv[t] = S->pinv[t]; }
     for (int qq = tid; qq < nq; qq += nt) {
@@ -711,20 +726,21 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
         sOrig[qq] = orig;
         sSlot[qq] = slot;
     }
+    cp_async_wait_prior<1>();                         // the tile (the C values may still fly)
     __syncthreads();
     {
         // 16 independent loads in flight per thread for Linv and for X
         const int u = tid & 63, t0 = tid >> 6;          // 4 row groups
         uint32_t lv[16], xv[16];
         const int slot = sSlot[u];
-        const int orig = sOrig[u];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int t = t0 + 4 * k;
             lv[k] = (t < rs && u < rs) ? S->Linv[t][u] : 0u;
             xv[k] = 0u;
+            // a position that is not displaced holds its own column (orig == q)
             if (t < rs && u < nq)
-                xv[k] = (slot >= 0) ? S->Dorig[slot][sProf[t]] : A[(a + sProf[t]) * lda + col0 + orig];
+                xv[k] = (slot >= 0) ? S->Dorig[slot][sProf[t]] : sTile[sProf[t]][u];
         }
         if (TCL == 0) {
 #pragma unroll
@@ -734,7 +750,6 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
             }
         } else {
             // digit planes: Linv row-major (k = u contiguous), X transposed (n = u rows, k = t contiguous)
-            extern __shared__ __align__(16) uint8_t fdyn[];
             __nv_bfloat16 *Ld = (__nv_bfloat16 *)fdyn;
             __nv_bfloat16 *Xt = Ld + TL * CUP_BMAX * FIN_LD;
 #pragma unroll
@@ -757,7 +772,6 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, const Dyn col0d,
         // columns 32 nh .. + 31 (four 16 x 8 tiles); shift s = i + j collects the digit
         // products A_i B_j
         constexpr int NS = 2 * TL - 1;
-        extern __shared__ __align__(16) uint8_t fdyn[];
         const __nv_bfloat16 *Ld = (const __nv_bfloat16 *)fdyn;
         const __nv_bfloat16 *Xt = Ld + TL * CUP_BMAX * FIN_LD;
         const int warp = tid >> 5, lane = tid & 31;
@@ -1157,39 +1171,49 @@ cudaError_t launch_slab_pivots(const uint32_t *A, int64_t lda, int64_t a, int br
     return cudaGetLastError();
 }
 
-cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, Dyn col0, int64_t n, ModP M,
+cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int brows, Dyn col0, int64_t n, ModP M,
                                const SlabScratch *S, int *err, cudaStream_t st, bool tensor)
 {
     const int64_t wmax = n - col0.lo;
     int64_t nb = (wmax + CUP_QT - 1) / CUP_QT;
     if (nb <= 0) return cudaSuccess;
+    if (brows < 1 || brows > CUP_BMAX) return cudaErrorInvalidValue;
+    // dynamic shared memory: the digit planes (tensor modes), then the slab tile
+    constexpr int tile = CUP_BMAX * CUP_QT * 4;
+    auto smem_of = [](int l) { return 2 * l * CUP_BMAX * FIN_LD * 2 + tile; };
+    static PerDeviceOnce attr;
+    const cudaError_t e = once_per_device(attr, [&] {
+        cudaError_t e2 = cudaFuncSetAttribute(k_slab_finish<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of(0));
+        if (e2 == cudaSuccess)
+            e2 = cudaFuncSetAttribute(k_slab_finish<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of(0));
+        if (e2 == cudaSuccess)
+            e2 = cudaFuncSetAttribute(k_slab_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of(1));
+        if (e2 == cudaSuccess)
+            e2 = cudaFuncSetAttribute(k_slab_finish<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of(2));
+        if (e2 == cudaSuccess)
+            e2 = cudaFuncSetAttribute(k_slab_finish<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of(3));
+        return e2;
+    });
+    if (e != cudaSuccess) return e;
     const uint32_t p = M.p;
+    SlabScratch *Sm = const_cast<SlabScratch *>(S);
     if (tensor && p < (1u << 24)) {
         // tensor-core product of l-limb digits; the recombined value is below 2^55 in size
         const int l = p < (1u << 8) ? 1 : p < (1u << 16) ? 2 : 3;
         const uint64_t off = ((1ull << 55) / p + 1) * p;
-        const int smem = 2 * l * CUP_BMAX * FIN_LD * 2;
-        static PerDeviceOnce attr;
-        const cudaError_t e = once_per_device(attr, [] {
-            cudaError_t e2 = cudaFuncSetAttribute(k_slab_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 1 * CUP_BMAX * FIN_LD * 2);
-            if (e2 == cudaSuccess)
-                e2 = cudaFuncSetAttribute(k_slab_finish<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 2 * CUP_BMAX * FIN_LD * 2);
-            if (e2 == cudaSuccess)
-                e2 = cudaFuncSetAttribute(k_slab_finish<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 3 * CUP_BMAX * FIN_LD * 2);
-            return e2;
-        });
-        if (e != cudaSuccess) return e;
-        SlabScratch *Sm = const_cast<SlabScratch *>(S);
-        if (l == 1) return launch_pdl(k_slab_finish<2>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
-        if (l == 2) return launch_pdl(k_slab_finish<3>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
-        return launch_pdl(k_slab_finish<4>, (unsigned)nb, 256, smem, st, A, lda, a, col0, n, M, Sm, err, off);
-        return cudaGetLastError();
+        if (l == 1)
+            return launch_pdl(k_slab_finish<2>, (unsigned)nb, 256, smem_of(1), st, A, lda, a, brows, col0, n, M, Sm, err, off);
+        if (l == 2)
+            return launch_pdl(k_slab_finish<3>, (unsigned)nb, 256, smem_of(2), st, A, lda, a, brows, col0, n, M, Sm, err, off);
+        return launch_pdl(k_slab_finish<4>, (unsigned)nb, 256, smem_of(3), st, A, lda, a, brows, col0, n, M, Sm, err, off);
     }
     // a row of Linv times a column of X sums CUP_BMAX products: wide sums unless CUP_BMAX (p-1)^2 < 2^64
     const bool wide = (long double)CUP_BMAX * (M.p - 1) * (long double)(M.p - 1) >= 18446744073709551615.0L;
-    SlabScratch *Sm = const_cast<SlabScratch *>(S);
-    if (wide) return launch_pdl(k_slab_finish<1>, (unsigned)nb, 256, 0, st, A, lda, a, col0, n, M, Sm, err, (uint64_t)0);
-    return launch_pdl(k_slab_finish<0>, (unsigned)nb, 256, 0, st, A, lda, a, col0, n, M, Sm, err, (uint64_t)0);
+    if (wide)
+        return launch_pdl(k_slab_finish<1>, (unsigned)nb, 256, smem_of(0), st, A, lda, a, brows, col0, n, M, Sm, err,
+                          (uint64_t)0);
+    return launch_pdl(k_slab_finish<0>, (unsigned)nb, 256, smem_of(0), st, A, lda, a, brows, col0, n, M, Sm, err,
+                      (uint64_t)0);
 }
 
 cudaError_t launch_swaplist(const int64_t *ipiv, Dyn k0, Dyn k1, int2 *pairs, int *count, cudaStream_t st)
