@@ -121,8 +121,11 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         s_Sfwd[CUP_BMAX], s_Spinv[CUP_BMAX + 1];
     __shared__ __align__(16) uint32_t s_coef[CUP_BMAX][PIV_PB];   // -a_kt of the block update, per row below a panel
     __shared__ int s_c, s_ext, s_fast;
+    __shared__ unsigned long long s_key;
     __shared__ int s_state[2][6];              // after each panel: rank, stop, spec count, done, rows to update, swaps
     __shared__ uint32_t s_T[PIV_PB][PIV_PB];   // fast panel path: the panel's row operations (fraction-free)
+    __shared__ uint32_t s_B[PIV_PB][PIV_PB];   // ... with dependent rows: the eliminated block, kept until verified
+    __shared__ int s_dep, s_bpf;                // ... with dependent rows: their mask, and the panel's pivot count
     __shared__ uint32_t s_sprod;
     __shared__ int s_slot[CUP_WNMAX + 1], s_sorig[CUP_WNMAX + 2];
 
@@ -149,25 +152,54 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     // Leading rows while the slab has no pivot (whole CTA): a row whose window
     // is zero is either a zero row or has its first nonzero beyond the window,
     // whose column then moves to position 0 (no elimination has happened yet,
-    // so the rows are still the unreduced input).
+    // so the rows are still the unreduced input). Unless row 0 has a nonzero in its
+    // window, all rows are examined at once: the first row with a nonzero in its window
+    // (from shared memory), then, among the rows before it, the first one with a nonzero
+    // beyond the window and that row's first such column, in one pass over those rows in
+    // global memory (32 loads of each lane in flight together; a slab of dependent rows
+    // is all such rows).
     int p0 = 0;
-    for (; p0 < brows; ++p0) {
-        int c = window_search(W + p0 * PIV_LDW, 0, wne, lane);
-        if (c >= 0) break;
-        if ((int64_t)wne == w) continue;                   // zero row
-        if (tid == 0) s_c = INT_MAX;
+    if (window_search(W, 0, wne, lane) < 0) {            // row 0's window is zero (same in every warp)
+        if (tid == 0) { s_c = brows; s_key = ~0ull; }
         __syncthreads();
-        const uint32_t *row = A + (a + p0) * lda + col0;
-        for (int64_t q = wne + tid; q < w; q += nt)
-            if (row[q]) { atomicMin(&s_c, (int)q); break; }
+        for (int i = warp; i < brows; i += nw)
+            if (window_search(W + i * PIV_LDW, 0, wne, lane) >= 0 && lane == 0) atomicMin(&s_c, i);
         __syncthreads();
-        c = s_c;
-        __syncthreads();
-        if (c == INT_MAX) continue;                        // zero row
-        for (int ii = tid; ii < brows; ii += nt) W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
-        if (tid == 0) { s_ext = c; s_wcol[0] = c; }
-        __syncthreads();
-        break;
+        p0 = s_c;
+        if ((int64_t)wne < w && p0 > 0) {
+            // warp w scans rows w, w + nw, ... below p0 beyond the window, 1024 columns a batch;
+            // each lane keeps its first nonzero column, the CTA the smallest (row, column)
+            const int span = (int)(w - wne);
+            unsigned long long best = ~0ull;
+            for (int i = warp; i < p0; i += nw) {
+                const uint32_t *row = A + (a + i) * lda + col0 + wne;
+                for (int qb = 0; qb < span; qb += 32 * 32) {
+                    uint32_t v[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int q = qb + 32 * j + lane;
+                        v[j] = q < span ? row[q] : 0u;
+                    }
+                    int first = INT_MAX;
+#pragma unroll
+                    for (int j = 31; j >= 0; --j) first = v[j] ? qb + 32 * j + lane : first;
+                    if (first != INT_MAX) {
+                        const unsigned long long key = ((unsigned long long)i << 32) | (unsigned long long)(wne + first);
+                        best = key < best ? key : best;
+                    }
+                }
+            }
+            if (best != ~0ull) atomicMin(&s_key, best);
+            __syncthreads();
+            const unsigned long long key = s_key;
+            if (key != ~0ull) {
+                const int c = (int)(key & 0xffffffffu);
+                p0 = (int)(key >> 32);
+                for (int ii = tid; ii < brows; ii += nt) W[ii * PIV_LDW + 0] = A[(a + ii) * lda + col0 + c];
+                if (tid == 0) { s_ext = c; s_wcol[0] = c; }
+                __syncthreads();
+            }
+        }
     }
     const int ext0 = s_ext;
 
@@ -237,7 +269,77 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
             if (lane < PIV_PB) s_Sfwd[br0 + lane] = Sx;
             if (lane == 0) s_sprod = Sall;
         }
-        if (lane == 0) s_fast = ok ? 1 : 0;
+        if (lane == 0) s_fast = ok ? 1 : 3;
+    };
+    // The same steps when a pivot was zero: row i's candidate is its value at the next rank
+    // position rr (the count of pivots so far). If that value is zero and the row's whole
+    // block residual (positions >= rr) is zero too, the row is taken as dependent: it
+    // takes no rank position and no step. The rest of its window residual is checked
+    // when the panel's row operations are applied (speculated rows beyond the window go to
+    // the finish kernel's check, as in the stepwise path). A zero candidate with a nonzero
+    // elsewhere in the block needs a transposition: s_fast = 0 sends the panel to the
+    // stepwise path. The block is left in s_B until the check has passed (s_fast = 2).
+    auto block_elim_dep = [&](const int bp0, const int br0) {
+        const int k = lane >> 2, jg = lane & 3, ja = 2 * jg, jb = ja + 1;
+        uint32_t b0 = W[(bp0 + k) * PIV_LDW + br0 + ja];
+        uint32_t b1 = W[(bp0 + k) * PIV_LDW + br0 + jb];
+        uint32_t t0 = (k == ja) ? one : 0u, t1 = (k == jb) ? one : 0u;
+        uint32_t fv = 0u, prow = 0u;           // lane t keeps the pivot of step t and its row
+        unsigned dmask = 0u;
+        int rr = 0;
+        bool bail = false;
+#pragma unroll
+        for (int i = 0; i < PIV_PB; ++i) {
+            const uint32_t src = (rr & 1) ? b1 : b0;
+            const uint32_t f = __shfl_sync(0xffffffffu, src, 4 * i + (rr >> 1));
+            if (f != 0u) {                      // the same in every lane
+                const uint32_t mk = __shfl_sync(0xffffffffu, src, 4 * k + (rr >> 1));
+                const uint32_t y0 = __shfl_sync(0xffffffffu, b0, 4 * i + jg), y1 = __shfl_sync(0xffffffffu, b1, 4 * i + jg);
+                const uint32_t z0 = __shfl_sync(0xffffffffu, t0, 4 * i + jg), z1 = __shfl_sync(0xffffffffu, t1, 4 * i + jg);
+                fv = (lane == rr) ? f : fv;
+                prow = (lane == rr) ? (uint32_t)i : prow;
+                const uint32_t n0 = ff<MONT>(f, b0, mk, y0, M), n1 = ff<MONT>(f, b1, mk, y1, M);
+                const uint32_t u0 = ff<MONT>(f, t0, mk, z0, M), u1 = ff<MONT>(f, t1, mk, z1, M);
+                const bool rk = k > i;
+                b0 = (rk && ja > rr) ? n0 : b0;
+                b1 = (rk && jb > rr) ? n1 : b1;
+                t0 = rk ? u0 : t0;
+                t1 = rk ? u1 : t1;
+                ++rr;
+            } else {
+                const bool nz = (k == i) && ((ja >= rr && b0 != 0u) || (jb >= rr && b1 != 0u));
+                if (__any_sync(0xffffffffu, nz)) { bail = true; break; }
+                dmask |= 1u << i;
+            }
+        }
+        // speculation is needed for dependent rows unless the window is the whole residual
+        if (!bail && (int64_t)wne < w && !speculate) bail = true;
+        if (!bail) {
+            s_B[k][ja] = b0;
+            s_B[k][jb] = b1;
+            s_T[k][ja] = (MONT && !WIDE) ? redc((uint64_t)t0 * M.r2, M) : t0;
+            s_T[k][jb] = (MONT && !WIDE) ? redc((uint64_t)t1 * M.r2, M) : t1;
+            if (lane < rr) {
+                s_f[br0 + lane] = fv;
+                s_pos[br0 + lane] = (br0 + lane == 0 && ext0 >= 0) ? ext0 : br0 + lane;
+                s_prof[br0 + lane] = bp0 + (int)prow;
+            }
+            const uint32_t id = MONT ? redc((uint64_t)M.r2, M) : one;
+            uint32_t v = (lane < rr) ? fv : id;
+#pragma unroll
+            for (int o = 1; o < PIV_PB; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                const uint32_t pv = scale_mul<MONT>(v, u, M);
+                v = (lane >= o) ? pv : v;
+            }
+            uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+            ex = (lane == 0) ? id : ex;
+            const uint32_t Sx = scale_mul<MONT>(Sprod, ex, M);
+            const uint32_t Sall = scale_mul<MONT>(Sprod, __shfl_sync(0xffffffffu, v, PIV_PB - 1), M);
+            if (lane < rr) s_Sfwd[br0 + lane] = Sx;
+            if (lane == 0) { s_sprod = Sall; s_dep = (int)dmask; s_bpf = rr; }
+        }
+        if (lane == 0) s_fast = bail ? 0 : 2;
     };
     for (; p0 < brows && !done; p0 += PIV_PB, ++pc) {
         const int pend = p0 + PIV_PB < brows ? p0 + PIV_PB : brows;
@@ -252,19 +354,88 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
         // = T x panel rows before); one parallel pass applies T to the panel's other
         // columns, instead of np steps separated by barriers. A zero on the diagonal sends
         // this panel, and the rest of the slab, to the stepwise elimination below.
-        bool fast = false;
+        int code = -1;                         // 1: fast, 2: fast with dependent rows, 0: stepwise
         if (pre_done) {
             // warp 0 eliminated this panel's block while the others finished the last update
-            fast = s_fast != 0;
-            try_fast = fast;
+            code = s_fast;
             pre_done = false;
         } else if (try_fast && np == PIV_PB && r0 + np <= wne) {
             if (warp == 0) block_elim(p0, r0);
             __syncthreads();
-            fast = s_fast != 0;
-            try_fast = fast;
+            code = s_fast;
         }
-        if (fast) {
+        if (code == 3) {
+            if (warp == 0) block_elim_dep(p0, r0);
+            __syncthreads();
+            code = s_fast;
+        }
+        bool fast = code == 1 || code == 2;
+        if (code == 0) try_fast = false;
+        // one entry of a panel row after the panel: row kk of T times the rows before it
+        auto tval = [&](const int kk, const uint32_t (&x)[PIV_PB]) -> uint32_t {
+            if (MONT && !WIDE) {
+                // s_T holds T R; at most eight products, each below p^2, sum below p R
+                // (narrow sums mean p < 2^28.8), so one Montgomery reduction gives sum T x
+                uint64_t s0 = 0;
+#pragma unroll
+                for (int j = 0; j < PIV_PB; ++j)
+                    if (j <= kk) s0 += (uint64_t)s_T[kk][j] * x[j];
+                return redc(s0, M);
+            } else {
+                uint64_t s0 = 0, s1 = 0;      // at most four products below 2^62 in each
+#pragma unroll
+                for (int j = 0; j < PIV_PB; ++j) {
+                    if (j > kk) continue;
+                    if (j < 4) s0 += (uint64_t)s_T[kk][j] * x[j];
+                    else s1 += (uint64_t)s_T[kk][j] * x[j];
+                }
+                return addm(red64(s0, M), red64(s1, M), M);
+            }
+        };
+        if (code == 2) {
+            // Dependent rows: the panel's row operations are applied to the columns right of
+            // the block and to E, with every dependent row's window values checked to be zero,
+            // before anything is written; a nonzero sends the panel to the stepwise path with
+            // the slab untouched (the block is still in s_B).
+            const unsigned dmask = (unsigned)s_dep;
+            const int nwc = wne - (r0 + np), ncol = nwc + pend;    // ncol < CTA size
+            const int ci = nt - 1 - tid;
+            const bool col = ci < ncol;
+            const bool inw = ci < nwc;
+            uint32_t *base = inw ? W + r0 + np + ci : E + (ci - nwc);
+            const int st = inw ? PIV_LDW : PIV_LDE;
+            uint32_t x[PIV_PB], res[PIV_PB];
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < PIV_PB; ++j) x[j] = col ? base[(p0 + j) * st] : 0u;
+#pragma unroll
+            for (int kk = 0; kk < PIV_PB; ++kk) {
+                res[kk] = kk == 0 ? x[0] : tval(kk, x);
+                if (col && inw && ((dmask >> kk) & 1u) && res[kk] != 0u) bad = true;
+            }
+            if (__syncthreads_or(bad)) {
+                fast = false;
+                try_fast = false;
+            } else {
+                if (col) {
+#pragma unroll
+                    for (int kk = 1; kk < PIV_PB; ++kk) base[(p0 + kk) * st] = res[kk];
+                }
+                if (tid < PIV_PB * PIV_PB) W[(p0 + (tid >> 3)) * PIV_LDW + r0 + (tid & 7)] = s_B[tid >> 3][tid & 7];
+                if ((int64_t)wne < w) {
+                    // speculated dependent rows, checked over the whole width by the finish kernel
+                    if (tid == 0) {
+                        int q = nspec;
+                        for (int i = 0; i < PIV_PB; ++i)
+                            if ((dmask >> i) & 1u) s_spec[q++] = p0 + i;
+                    }
+                    nspec += __popc(dmask);
+                }
+                r = r0 + s_bpf;
+                Sprod = s_sprod;
+                __syncthreads();
+            }
+        } else if (fast) {
             // window positions right of the block, then E columns [0, pend): thread per column,
             // panel rows 1 .. np-1 as sums of T's entries times the rows' values before the panel.
             // Columns go to the last threads, whose warps the multiplier pass below leaves
@@ -308,7 +479,8 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
             if (pend >= brows) __syncthreads();
             r = r0 + np;
             Sprod = s_sprod;
-        } else {
+        }
+        if (!fast) {
         if (warp < PIV_PW) {
             // Panel of rows [p0, pend), eliminated by the first PIV_PW warps (named
             // barrier 1): the rows are taken one by one as in the unblocked
