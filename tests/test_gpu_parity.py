@@ -247,3 +247,56 @@ def test_factor_host_speculation_fallback(cuda_lib):
     assert r == d["rank"]
     assert np.array_equal(hA.numpy().view(np.uint32).astype(np.int64), d["packed"])
     h.close()
+
+
+def _dependent_tail(m, n, r, p, seed):
+    """Rank r, the first rows independent and every later row a combination of them: after r
+    pivots every slab is made of dependent rows whose residual beyond the window is zero."""
+    rng = np.random.default_rng(seed)
+    X = rng.integers(0, p, size=(r, r))
+    Y = rng.integers(0, p, size=(r, n))
+    top = inputs.matmul_mod(X, Y, p)
+    Z = rng.integers(0, p, size=(m - r, r))
+    return np.vstack([top, inputs.matmul_mod(Z, top, p)]).astype(np.uint32)
+
+
+def _late_nonzeros(m, n, p, seed):
+    """Rows whose first nonzero lies beyond a pivot window (zero in the first 150 columns)
+    ahead of ordinary rows, zero rows among them, so that a slab's leading rows move a
+    column from beyond the window to its first position."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(0, p, size=(m, n))
+    lead = rng.random(m) < 0.4
+    A[lead, :150] = 0
+    A[rng.random(m) < 0.15] = 0
+    return A.astype(np.uint32)
+
+
+def _mixed_panels(m, n, p, seed):
+    """Independent rows with dependent ones interleaved (every third row a combination of
+    earlier rows, every seventh zero): most 8-row panels hold a row that takes no pivot."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(0, p, size=(m, n))
+    for i in range(m):
+        if i % 7 == 6:
+            A[i] = 0
+        elif i % 3 == 2:
+            c = rng.integers(0, p, size=i)
+            A[i] = (c @ A[:i]) % p
+    return A.astype(np.uint32)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("case", ["dependent_tail", "late_nonzeros", "mixed_panels"])
+@pytest.mark.parametrize("p", [251, 65521, 8388593])
+def test_factor_dependent_rows(cuda_lib, engine, case, p):
+    """Slabs made of dependent rows (the scan beyond the window), leading rows whose first
+    nonzero is beyond the window, and panels mixing dependent and independent rows (the
+    fast path with rows that take no rank position), against the oracle."""
+    if case == "dependent_tail":
+        A = _dependent_tail(640, 300, 90, p, seed=p % 97)
+    elif case == "late_nonzeros":
+        A = _late_nonzeros(400, 320, p, seed=p % 89)
+    else:
+        A = _mixed_panels(300, 260, p, seed=p % 83)
+    _factor_case(cuda_lib, A, p, engine=engine, window=64)
