@@ -101,10 +101,13 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
               int64_t n, int wn, int speculate, ModP M, SlabScratch *__restrict__ S,
               int64_t *__restrict__ g_ipiv, int64_t *__restrict__ g_prof, int64_t *__restrict__ rank_next)
 {
-    pdl_enter();
+    // col0 was written by the leaf before (several launches back), so it and the work on
+    // shared memory alone (E's identity, the window's column map) precede the dependency
+    // wait; the window itself comes from the Schur update just before
     const int64_t col0 = col0d.eval();
     const int64_t w = n - col0;
     if (w <= 0) {
+        pdl_enter();
         // every column is already a pivot: the slab's rows are dependent
         if (threadIdx.x == 0) {
             S->r_s = 0; S->i_stop = brows; S->wne = 0; S->ext_pos = -1; S->ext_slot = -1;
@@ -135,18 +138,19 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     // R^{-1} for the Montgomery variant (the factor each fraction-free update carries), else 1
     const uint32_t rinv = MONT ? redc(1ull, M) : one;
 
+    for (int idx = tid; idx < brows * CUP_BMAX; idx += nt) {
+        const int i = idx >> 6, j = idx & (CUP_BMAX - 1);
+        E[i * PIV_LDE + j] = (i == j) ? one : 0u;
+    }
+    for (int q = tid; q < wne; q += nt) s_wcol[q] = q;
+    if (tid == 0) s_ext = -1;
+    pdl_enter();
     // window: every element copied asynchronously, one memory latency for the tile
     for (int i = warp; i < brows; i += nw) {
         const uint32_t *src = A + (a + i) * lda + col0;
         for (int q = lane; q < wne; q += 32) cp_async4(W + i * PIV_LDW + q, src + q);
     }
-    for (int idx = tid; idx < brows * CUP_BMAX; idx += nt) {
-        const int i = idx >> 6, j = idx & (CUP_BMAX - 1);
-        E[i * PIV_LDE + j] = (i == j) ? one : 0u;
-    }
     cp_async_wait_all();
-    for (int q = tid; q < wne; q += nt) s_wcol[q] = q;
-    if (tid == 0) s_ext = -1;
     __syncthreads();
 
     // Leading rows while the slab has no pivot (whole CTA): a row whose window
@@ -875,6 +879,16 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const
     __shared__ uint32_t sPinv[CUP_BMAX];
     __shared__ int sOrig[CUP_QT], sSlot[CUP_QT], sProf[CUP_BMAX];
 
+    // Every read of the scratch is issued at once (its arrays have fixed sizes, so each
+    // read is in bounds); the slab's counts only select among the values afterwards.
+    const int u = tid & 63, t0 = tid >> 6;          // 4 row groups
+    uint32_t lv[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) lv[k] = S->Linv[t0 + 4 * k][u];
+    int prof_v = 0, wcol_v = 0, wslot_v = -1;
+    uint32_t pinv_v = 0u;
+    if (tid < CUP_BMAX) { prof_v = S->prof[tid]; pinv_v = S->pinv[tid]; }
+    if (tid < CUP_QT && q0 + tid < CUP_WNMAX) { wcol_v = S->win_col[q0 + tid]; wslot_v = S->win_slot[q0 + tid]; }
     const int rs = S->r_s, stop = S->i_stop, wne = S->wne;
     const int ext_pos = S->ext_pos, ext_slot = S->ext_slot;
     if (TCL > 0 && q0 == 0) {
@@ -888,27 +902,26 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const
     }
     cp_async_commit();
 
-    for (int t = tid; t < rs; t += nt) { sProf[t] = S->prof[t]; sPinv[t] = S->pinv[t]; }
-    for (int qq = tid; qq < nq; qq += nt) {
-        int64_t q = q0 + qq;
+    if (tid < rs) { sProf[tid] = prof_v; sPinv[tid] = pinv_v; }      // rs <= CUP_BMAX <= blockDim
+    if (tid < nq) {
+        const int64_t q = q0 + tid;
         int orig, slot;
-        if (q < wne) { orig = S->win_col[q]; slot = S->win_slot[q]; }
+        if (q < wne) { orig = wcol_v; slot = wslot_v; }
         else if (q == ext_pos) { orig = 0; slot = ext_slot; }
         else { orig = (int)q; slot = -1; }
-        sOrig[qq] = orig;
-        sSlot[qq] = slot;
+        sOrig[tid] = orig;
+        sSlot[tid] = slot;
     }
     cp_async_wait_prior<1>();                         // the tile (the C values may still fly)
     __syncthreads();
     {
-        // 16 independent loads in flight per thread for Linv and for X
-        const int u = tid & 63, t0 = tid >> 6;          // 4 row groups
-        uint32_t lv[16], xv[16];
+        // X from the tile (or the displaced values), Linv as read above
+        uint32_t xv[16];
         const int slot = sSlot[u];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int t = t0 + 4 * k;
-            lv[k] = (t < rs && u < rs) ? S->Linv[t][u] : 0u;
+            lv[k] = (t < rs && u < rs) ? lv[k] : 0u;
             xv[k] = 0u;
             // a position that is not displaced holds its own column (orig == q)
             if (t < rs && u < nq)
