@@ -1090,27 +1090,39 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const
             if (i0 + 4 * k < stop && t < rs) sL[i0 + 4 * k][t] = cv[k];
     }
     __syncthreads();
-    // rows: U rows col0 + t (t < rs), then slab rows a + i (i < stop) that are not U rows
-    const int nrow = rs + stop;
-    const int qq = tid & (CUP_QT - 1);
-#pragma unroll 4
-    for (int k = tid >> 6; k < nrow; k += nt >> 6) {
-        if (qq >= nq) continue;
-        int64_t q = q0 + qq;
-        int64_t rho;
-        uint32_t v;
-        if (k < rs) {
-            rho = col0 + k;
-            if (q > k) v = sX[k][qq];
-            else if (rho >= a) v = (q < rs) ? sL[rho - a][q] : 0u;
-            else v = 0u;
-        } else {
-            int i = k - rs;
-            rho = a + i;
-            if (rho < col0 + rs) continue;     // written above as a U row
-            v = (q < rs) ? sL[i][q] : 0u;
+    // rows: U rows col0 + t (t < rs), then slab rows a + i (i < stop) that are not U rows.
+    // Thread (column qq, row group g; 256 threads) takes rows g + 4 j of each kind: all 16
+    // values of a kind are gathered from shared memory before its stores (indices clamped
+    // into the arrays, the selections made on the values).
+    {
+        const int qq = tid & (CUP_QT - 1), g = tid >> 6;
+        if (qq < nq) {
+            const int64_t q = q0 + qq;
+            const int qc = q < rs ? (int)q : 0;
+            uint32_t *colp = A + col0 + q;
+            uint32_t vu[16], vs[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = g + 4 * j;
+                const int64_t rho = col0 + k;
+                const int ri = rho >= a ? (int)(rho - a) : 0;
+                const uint32_t x = sX[k][qq], c = sL[ri][qc];
+                vu[j] = (q > k) ? x : (rho >= a && q < rs) ? c : 0u;
+                const uint32_t cs = sL[k][qc];
+                vs[j] = q < rs ? cs : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = g + 4 * j;
+                if (k < rs) colp[(col0 + k) * lda] = vu[j];
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int i = g + 4 * j;
+                const int64_t rho = a + i;
+                if (i < stop && rho >= col0 + rs) colp[rho * lda] = vs[j];
+            }
         }
-        A[rho * lda + col0 + q] = v;
     }
 }
 
