@@ -764,22 +764,35 @@ k_slab_pivots(const uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows,
     // L^{-1}[t][u] = E[prof t][prof u] / f_t (zero for u > t). For odd p the
     // factors are Montgomery representations (Sinv R, and f^{-1} R = mu^{-1}),
     // so each entry is one Montgomery step.
+    // (512 threads: column t or u = tid % 64, rows g + 8 j for the row group g = tid / 64;
+    // each thread's eight values are read from shared memory before any is stored)
     {
-        const int t = tid & (CUP_BMAX - 1);
+        const int t = tid & (CUP_BMAX - 1), g = tid >> 6;
         if (t < rs) {
             const int pt = s_prof[t];
             const uint32_t sinv = s_Sinv[t];
-            for (int i = tid >> 6; i < stop; i += nt >> 6) {
-                const uint32_t wv = W[i * PIV_LDW + t];
-                S->Cn[i][t] = (i >= pt) ? (MONT ? redc((uint64_t)wv * sinv, M) : mulm(wv, sinv, M)) : 0u;
+            uint32_t wv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) wv[j] = W[(g + 8 * j) * PIV_LDW + t];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int i = g + 8 * j;
+                if (i < stop)
+                    S->Cn[i][t] = (i >= pt) ? (MONT ? redc((uint64_t)wv[j] * sinv, M) : mulm(wv[j], sinv, M)) : 0u;
             }
-        }
-        const int u = tid & (CUP_BMAX - 1);
-        if (u < rs) {
-            const int pu = s_prof[u];
-            for (int t2 = tid >> 6; t2 < rs; t2 += nt >> 6) {
-                const uint32_t ev = E[s_prof[t2] * PIV_LDE + pu];
-                S->Linv[t2][u] = MONT ? redc((uint64_t)ev * s_muinv[t2], M) : mulm(ev, s_finv[t2], M);
+            const int pu = pt;                 // the same column, as u
+            uint32_t ev[8], mv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int t2 = g + 8 * j;
+                const int pr = t2 < rs ? s_prof[t2] : 0;
+                ev[j] = E[pr * PIV_LDE + pu];
+                mv[j] = MONT ? s_muinv[t2] : s_finv[t2];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int t2 = g + 8 * j;
+                if (t2 < rs) S->Linv[t2][t] = MONT ? redc((uint64_t)ev[j] * mv[j], M) : mulm(ev[j], mv[j], M);
             }
         }
     }
@@ -867,7 +880,7 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nq = (int)((w - q0) < CUP_QT ? (w - q0) : CUP_QT);
     extern __shared__ __align__(16) uint8_t fdyn[];
-    uint32_t (*sTile)[CUP_QT] = (uint32_t (*)[CUP_QT])(fdyn + (TCL > 0 ? 2 * TCL * CUP_BMAX * FIN_LD * 2 : 0));
+    uint32_t (*sTile)[CUP_QT + 1] = (uint32_t (*)[CUP_QT + 1])(fdyn + (TCL > 0 ? 2 * TCL * CUP_BMAX * FIN_LD * 2 : 0));
     for (int idx = tid; idx < brows * CUP_QT; idx += nt) {
         const int i = idx >> 6, qq = idx & (CUP_QT - 1);
         if (qq < nq) cp_async4(&sTile[i][qq], A + (a + i) * lda + col0 + q0 + qq);
@@ -915,40 +928,61 @@ k_slab_finish(uint32_t *__restrict__ A, int64_t lda, int64_t a, int brows, const
     cp_async_wait_prior<1>();                         // the tile (the C values may still fly)
     __syncthreads();
     {
-        // X from the tile (or the displaced values), Linv as read above
-        uint32_t xv[16];
-        const int slot = sSlot[u];
+        // X from the tile (or the displaced values; a position that is not displaced holds
+        // its own column), Linv as read above
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int t = t0 + 4 * k;
             lv[k] = (t < rs && u < rs) ? lv[k] : 0u;
-            xv[k] = 0u;
-            // a position that is not displaced holds its own column (orig == q)
-            if (t < rs && u < nq)
-                xv[k] = (slot >= 0) ? S->Dorig[slot][sProf[t]] : sTile[sProf[t]][u];
         }
         if (TCL == 0) {
+            const int slot = sSlot[u];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                sL[t0 + 4 * k][u] = lv[k];
-                sX[t0 + 4 * k][u] = xv[k];
+                const int t = t0 + 4 * k;
+                uint32_t xv = 0u;
+                if (t < rs && u < nq) xv = (slot >= 0) ? S->Dorig[slot][sProf[t]] : sTile[sProf[t]][u];
+                sL[t][u] = lv[k];
+                sX[t][u] = xv;
             }
         } else {
-            // digit planes: Linv row-major (k = u contiguous), X transposed (n = u rows, k = t contiguous)
+            // digit planes: Linv row-major (k = u contiguous), X transposed (n = u rows, k = t
+            // contiguous). X is taken by warp w for columns w + 8 m with the lanes along t, so
+            // its transposed stores are consecutive (the tile's rows are padded to 65 words,
+            // so reading a column of it is conflict-free too).
             __nv_bfloat16 *Ld = (__nv_bfloat16 *)fdyn;
             __nv_bfloat16 *Xt = Ld + TL * CUP_BMAX * FIN_LD;
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const int t = t0 + 4 * k;
-                __nv_bfloat16 dl[TL], dx[TL];
+                __nv_bfloat16 dl[TL];
                 limb_digits<TL>(lv[k], M.p, dl);
-                limb_digits<TL>(xv[k], M.p, dx);
 #pragma unroll
-                for (int l = 0; l < TCL; ++l) {
-                    Ld[(l * CUP_BMAX + t) * FIN_LD + u] = dl[l];
-                    Xt[(l * CUP_BMAX + u) * FIN_LD + t] = dx[l];
+                for (int l = 0; l < TCL; ++l) Ld[(l * CUP_BMAX + t) * FIN_LD + u] = dl[l];
+            }
+            const int wx = tid >> 5, lx = tid & 31;
+            uint32_t xw[16];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int u2 = wx + 8 * m, slot2 = sSlot[u2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int t2 = lx + 32 * h;
+                    const int pr = t2 < rs ? sProf[t2] : 0;
+                    uint32_t x = 0u;
+                    if (t2 < rs && u2 < nq) x = (slot2 >= 0) ? S->Dorig[slot2][pr] : sTile[pr][u2];
+                    xw[2 * m + h] = x;
                 }
             }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    __nv_bfloat16 dx[TL];
+                    limb_digits<TL>(xw[2 * m + h], M.p, dx);
+#pragma unroll
+                    for (int l = 0; l < TCL; ++l) Xt[(l * CUP_BMAX + wx + 8 * m) * FIN_LD + lx + 32 * h] = dx[l];
+                }
         }
     }
     __syncthreads();
@@ -1376,7 +1410,7 @@ cudaError_t launch_slab_finish(uint32_t *A, int64_t lda, int64_t a, int brows, D
     if (nb <= 0) return cudaSuccess;
     if (brows < 1 || brows > CUP_BMAX) return cudaErrorInvalidValue;
     // dynamic shared memory: the digit planes (tensor modes), then the slab tile
-    constexpr int tile = CUP_BMAX * CUP_QT * 4;
+    constexpr int tile = CUP_BMAX * (CUP_QT + 1) * 4;
     auto smem_of = [](int l) { return 2 * l * CUP_BMAX * FIN_LD * 2 + tile; };
     static PerDeviceOnce attr;
     const cudaError_t e = once_per_device(attr, [&] {
