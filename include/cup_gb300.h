@@ -71,7 +71,7 @@ enum {
                                   (reads each block's rank back before launching the next) */
     CUP_OPT_INT_PATH = 7,      /* images of cup_int_det / cup_int_rank: 0 (default) by a cost model,
                                   1 the batched launch (min(m, n) <= 2048), 2 one full-device CUP per prime */
-    CUP_OPT_SHORT_K = 8        /* tensor-engine Schur updates with K at most this (0..128, default 128),
+    CUP_OPT_SHORT_K = 8        /* tensor-engine Schur updates with K at most this (0..256, default 128),
                                   p < 2^24 and at most 2^21 entries of C run as one launch of
                                   mma.sync digit products formed in shared memory instead of a digit
                                   split plus a tcgen05 launch; 0 sends every update to tcgen05 */

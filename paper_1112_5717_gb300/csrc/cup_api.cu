@@ -32,7 +32,8 @@ struct cup_handle {
     int leaf_rows = 64;
     int window = 96;
     int64_t tc_min_k = 64;
-    int64_t short_k = SHORT_K_MAX;  // largest K of the one-launch short-K tensor update (0: never)
+    int64_t short_k = 128;          // largest K of the one-launch short-K tensor update (0: never;
+                                    // K = 256 is supported but measured slower than tcgen05 there)
     bool user_set[3] = {false, false, false};   // leaf_rows, window, tc_min_k set by cup_set_option
     struct TuneRule {
         int64_t limbs = -1, tall = -1, min_lo = 0, min_hi = INT64_MAX;

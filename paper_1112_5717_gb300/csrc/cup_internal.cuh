@@ -242,9 +242,10 @@ cudaError_t launch_det_reduce(const uint32_t *A, int64_t lda, int64_t n, const i
 int tc_limbs(uint32_t p);
 
 // One-launch short-K tensor update (cup_short.cu): mma.sync on digits made in
-// shared memory, for K <= SHORT_K_MAX, p < 2^24 and at most SHORT_MAX_OUTPUTS
-// entries of C (beyond that the tcgen05 path's throughput wins).
-#define SHORT_K_MAX 128
+// shared memory, for K up to the handle's bound (at most SHORT_K_MAX), p < 2^24
+// and at most SHORT_MAX_OUTPUTS entries of C (beyond that the tcgen05 path's
+// throughput wins).
+#define SHORT_K_MAX 256
 #define SHORT_MAX_OUTPUTS (1ll << 21)
 bool gemm_short_ok(uint32_t p, int64_t M, int64_t Nhi, int64_t Khi, int64_t kmax);
 cudaError_t launch_gemm_short_desc(const GemmDesc &d, ModP M, cudaStream_t st);
